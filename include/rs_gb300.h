@@ -1,0 +1,125 @@
+/*
+ * rs_gb300.h - C ABI of the GB300 (sm_103a) Reed-Solomon erasure-coding
+ * library: systematic RS(k, m) over GF(2^w), w in {8, 16}, in the
+ * polynomial realization of "On the Effectiveness of Polynomial Realization
+ * of Reed-Solomon Codes for Storage Systems" (§3), with the Vandermonde and
+ * Cauchy bit-matrix matrix realizations (§2) as peers.
+ *
+ * Conventions shared by every entry point
+ *   - Blocks: a stripe is k data blocks d_0..d_{k-1} and m parity blocks
+ *     p_0..p_{m-1} of `block_bytes` bytes each.  Block index b in [0, n),
+ *     n = k + m: b < k is d_b, b >= k is p_(b-k).  Symbol t of every block
+ *     forms one column (one codeword); w = 8 symbols are bytes, w = 16
+ *     symbols are little-endian 16-bit words.
+ *   - Pointers: every block pointer is a DEVICE pointer, 16-byte aligned,
+ *     owned by the caller.  Pointer arrays are HOST arrays, read during the
+ *     call only.  Input and output blocks must not overlap.
+ *   - Streams: `stream` is a cudaStream_t (NULL = legacy default stream).
+ *     Work is enqueued asynchronously; the call returns once it is enqueued.
+ *   - Errors: argument errors are detected on the host, return before any
+ *     work is enqueued and set a thread-local message (rs_last_error).  A
+ *     failed kernel launch returns RS_ECUDA.  Kernel-side timeouts of the
+ *     bounded shared-memory pipeline waits are reported through the code's
+ *     device status word (rs_poll_status).  No C++ exception crosses the ABI.
+ *   - Limits of the device path: n <= 64, m <= 8, n <= 2^w - 1.
+ */
+#ifndef RS_GB300_H
+#define RS_GB300_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct rs_code rs_code;
+typedef struct rs_batch rs_batch;
+
+typedef enum {
+  RS_POLY = 0,         /* generator polynomial g(x) = prod_{i<m}(x + alpha^i), §3 */
+  RS_VANDERMONDE = 1,  /* systematic Vandermonde generator matrix, §2.2 */
+  RS_CAUCHY = 2        /* Cauchy generator, bit-matrix XOR over packets, §2.3 */
+} rs_realization;
+
+typedef enum {
+  RS_OK = 0,
+  RS_EINVAL = 1,             /* bad argument (null, misaligned, bad size, bad index) */
+  RS_ETOOMANY_ERASURES = 2,  /* more erasures than parity blocks */
+  RS_ENOMEM = 3,             /* host or device allocation failed */
+  RS_ECUDA = 4,              /* a CUDA call failed */
+  RS_ETIMEOUT = 5,           /* a device-side bounded wait gave up */
+  RS_EUNSUPPORTED = 6        /* valid code outside the device path's limits */
+} rs_status;
+
+typedef enum {
+  RS_READ_MIN = 0,  /* decode reads the first k surviving blocks (by index) */
+  RS_READ_ALL = 1   /* decode reads every surviving block (§3.3, second remark) */
+} rs_read_mode;
+
+/* Library version (major * 10000 + minor * 100 + patch). */
+int rs_version(void);
+
+/* Message of the last failed call on this thread ("" if none).  The pointer
+ * stays valid until the next call on the same thread. */
+const char *rs_last_error(void);
+
+/* Create a code.  §3.1 (g(x)), §2.2 (Vandermonde), §2.3 (Cauchy).
+ *   k >= 1, m in [1, 8], k + m <= 64 and <= 2^w - 1, w in {8, 16},
+ *   realization in rs_realization.
+ * Builds the generator on the host and allocates a 4-byte device status
+ * word on the current device.  *out receives the code (owned by the caller,
+ * free with rs_destroy).  Errors: RS_EINVAL, RS_EUNSUPPORTED, RS_ENOMEM,
+ * RS_ECUDA. */
+rs_status rs_init(int k, int m, int w, int realization, rs_code **out);
+
+/* Free a code (NULL is ignored).  Work still queued on a stream that uses
+ * the code must have completed. */
+void rs_destroy(rs_code *code);
+
+/* Cauchy only: packet size P in bytes (§2.3 projection; default 2048).
+ * A block is a sequence of super-packets of w*P bytes; packet c of a
+ * super-packet holds bit c of its 8P symbols.  P must be a positive
+ * multiple of 16; block_bytes must then be a multiple of w*P. */
+rs_status rs_set_packet_bytes(rs_code *code, size_t packet_bytes);
+
+/* Which survivors a decode reads (rs_read_mode, default RS_READ_MIN). */
+rs_status rs_set_read_mode(rs_code *code, int mode);
+
+/* Launch shape used by this code's kernels: consumer warps per CTA (1..16,
+ * capped per kernel), shared-memory ring depth (2..64) and CTAs per SM
+ * (1..4).  0 keeps the current value.  Set by the autotuner. */
+rs_status rs_set_launch(rs_code *code, int consumer_warps, int depth, int ctas_per_sm);
+
+/* Encode one stripe: parity from data.  §3.2 Eq. 1 (polynomial: remainder of
+ * x^m d(x) divided by g(x)), §2.1 (matrix: parity rows of G times d).
+ *   data_ptrs: host array of k device pointers (read only);
+ *   parity_ptrs: host array of m device pointers (written);
+ *   block_bytes: bytes per block (any value >= 0; even for w = 16; a multiple
+ *   of w*P for RS_CAUCHY).  block_bytes = 0 is a no-op.
+ * Errors: RS_EINVAL (null code/pointer, misalignment, size), RS_ECUDA. */
+rs_status rs_encode(rs_code *code, const void *const *data_ptrs, void *const *parity_ptrs,
+                    size_t block_bytes, void *stream);
+
+/* Decode one stripe: rebuild the erased blocks.  §3.3 (polynomial: Step 1
+ * evaluates D(alpha^j) over the read survivors, Step 2 solves the small
+ * Vandermonde system, inverted once per erasure pattern on the host), §2.1
+ * (matrix realizations, solved here through the parity-check matrix).
+ *   erasures: host array of n_erasures distinct block indices in [0, n);
+ *   n_erasures in [0, m] (0 is a no-op, > m gives RS_ETOOMANY_ERASURES);
+ *   block_ptrs: host array of n device pointers; survivors are read, erased
+ *   blocks are written; block_bytes as for rs_encode.
+ * Errors: RS_EINVAL, RS_ETOOMANY_ERASURES, RS_ECUDA. */
+rs_status rs_decode(rs_code *code, const int *erasures, int n_erasures, void *const *block_ptrs,
+                    size_t block_bytes, void *stream);
+
+/* Read and clear the code's device status word (synchronises the device).
+ * *device_status receives 0 or the kernel's error code; the return value is
+ * RS_ETIMEOUT when the word was set, RS_OK otherwise. */
+rs_status rs_poll_status(rs_code *code, int *device_status);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* RS_GB300_H */

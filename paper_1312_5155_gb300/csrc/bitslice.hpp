@@ -1,0 +1,121 @@
+// Bit-sliced GF(2^w) arithmetic on 32 symbols at a time.
+//
+// A thread holds 32 symbols of one block as W 32-bit words (W = w: 8 words
+// = 32 bytes for GF(2^8), 16 words = 32 little-endian uint16 for GF(2^16)).
+// transpose_w() turns those words into W bit-planes: plane b holds bit b of
+// all 32 symbols.  In that form
+//   - adding symbols is one XOR per plane,
+//   - multiplying by a constant e is the GF(2) matrix of §2.3's bit-matrix
+//     projection applied to the planes: plane r of e*x is the XOR of the
+//     planes c with bit r of (e * alpha^c) set.
+// When e is known at compile time only the XORs for the ones of its matrix
+// are emitted; when it is a runtime value every (row, column) pair costs one
+// AND-XOR with a 0/~0 mask.
+//
+// The symbol-to-plane transpose is three (w=8) or four (w=16) rounds of
+// masked swaps between register pairs; each round exchanges one bit of the
+// register index with one bit of the position inside the word, so the whole
+// transpose is an involution and also converts planes back to symbols.
+// Plane b ends up with bit b of symbol (word v, lane i) at position
+// w*i + v (i = symbol within the 32-bit word).
+#pragma once
+#include "gf.hpp"
+
+namespace rsgb {
+
+// x[i], x[i+D] for all i with bit D clear: exchange the bits of x[i] above
+// the mask with the bits of x[i+D] below it.
+template <int N, int D, int S, uint32_t MASK>
+RS_HD void swap_round(uint32_t* x) {
+#pragma unroll
+  for (int i = 0; i < N; ++i) {
+    if ((i & D) == 0) {
+      const uint32_t lo = x[i], hi = x[i + D];
+#if defined(__CUDA_ARCH__)
+      if (S == 8) {
+        // byte-granular round: one PRMT per output word
+        x[i] = __byte_perm(lo, hi, 0x6240);
+        x[i + D] = __byte_perm(lo, hi, 0x7351);
+        continue;
+      }
+#endif
+      x[i] = (lo & MASK) | ((hi << S) & ~MASK);
+      x[i + D] = ((lo >> S) & MASK) | (hi & ~MASK);
+    }
+  }
+}
+
+template <int W>
+RS_HD void transpose(uint32_t* x);
+
+template <>
+RS_HD void transpose<8>(uint32_t* x) {
+  swap_round<8, 4, 4, 0x0F0F0F0Fu>(x);
+  swap_round<8, 2, 2, 0x33333333u>(x);
+  swap_round<8, 1, 1, 0x55555555u>(x);
+}
+
+template <>
+RS_HD void transpose<16>(uint32_t* x) {
+  swap_round<16, 8, 8, 0x00FF00FFu>(x);
+  swap_round<16, 4, 4, 0x0F0F0F0Fu>(x);
+  swap_round<16, 2, 2, 0x33333333u>(x);
+  swap_round<16, 1, 1, 0x55555555u>(x);
+}
+
+// acc ^= E * in   (E a compile-time field element)
+template <int W, uint32_t E>
+RS_HD void mul_acc(uint32_t* acc, const uint32_t* in) {
+  constexpr typename BitMatrix<W, E>::Rows M = BitMatrix<W, E>::value;
+#pragma unroll
+  for (int r = 0; r < W; ++r) {
+#pragma unroll
+    for (int c = 0; c < W; ++c) {
+      if ((M.r[r] >> c) & 1u) acc[r] ^= in[c];
+    }
+  }
+}
+
+// out = E * in
+template <int W, uint32_t E>
+RS_HD void mul_set(uint32_t* out, const uint32_t* in) {
+#pragma unroll
+  for (int r = 0; r < W; ++r) out[r] = 0;
+  mul_acc<W, E>(out, in);
+}
+
+// x = alpha * x in place: shift the planes up by one and fold the top plane
+// back in through the low bits of the primitive polynomial.
+template <int W>
+RS_HD void mul_alpha(uint32_t* x) {
+  constexpr uint32_t low = prim_poly(W) & ((1u << W) - 1u);
+  const uint32_t top = x[W - 1];
+#pragma unroll
+  for (int r = W - 1; r >= 1; --r) x[r] = x[r - 1];
+  x[0] = top;
+#pragma unroll
+  for (int r = 1; r < W; ++r) {
+    if ((low >> r) & 1u) x[r] ^= top;
+  }
+}
+
+// Runtime constant e given as W masks: mask[c] = ~0 if bit c of e is set.
+// acc ^= e * in, computed as sum_c bit_c(e) * (alpha^c * in).  `chain` is
+// clobbered (it walks in, alpha*in, alpha^2*in, ...).
+template <int W>
+RS_HD void mul_acc_masked(uint32_t* acc, uint32_t* chain, const uint32_t* mask) {
+#pragma unroll
+  for (int c = 0; c < W; ++c) {
+    const uint32_t mk = mask[c];
+#pragma unroll
+    for (int r = 0; r < W; ++r) acc[r] ^= chain[r] & mk;
+    if (c + 1 < W) mul_alpha<W>(chain);
+  }
+}
+
+// Masks of a runtime constant e (host side): mask[c] = -(bit c of e).
+RS_HD void expand_masks(uint32_t e, int w, uint32_t* mask) {
+  for (int c = 0; c < w; ++c) mask[c] = ((e >> c) & 1u) ? 0xFFFFFFFFu : 0u;
+}
+
+}  // namespace rsgb

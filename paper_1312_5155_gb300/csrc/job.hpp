@@ -1,0 +1,65 @@
+// Work description shared by the host planner and the kernels.
+//
+// A launch processes a list of stripe operations.  Every stripe is cut into
+// tiles of `slice_bytes` per block; tiles of all stripes are numbered
+// globally and CTAs take them round-robin.  For each tile the producer
+// streams one slice per input block (in the codec's consumption order)
+// through the shared-memory ring; consumers turn the slices into output
+// slices written straight to HBM.
+#pragma once
+#include <stdint.h>
+
+#include "gf.hpp"
+
+namespace rsgb {
+
+enum : uint8_t {
+  kOpEncode = 0,       // polynomial LFSR encode: inputs d_{k-1}..d_0, outputs p_0..p_{m-1}
+  kOpDecode = 1,       // polynomial Horner-syndrome decode
+  kOpMatEncode = 2,    // matrix realization encode (runtime coefficient masks)
+  kOpMatDecode = 3,    // matrix realization decode through H = [P | I]
+};
+
+enum : uint8_t { kLayoutSymbol = 0, kLayoutPacket = 1 };
+
+struct StripeDesc {
+  uint64_t bytes;       // block bytes B
+  uint64_t read_mask;   // decode: bit p set = position / block p is read
+  uint32_t tile_begin;  // first global tile index of this stripe
+  uint32_t ptr_off;     // first pointer: n_in inputs, then n_out outputs
+  uint32_t coef_off;    // coefficient masks (words) for runtime matrices
+  uint16_t n_in;        // input blocks streamed per tile
+  uint16_t n_out;       // output blocks written per tile
+  uint8_t op;
+  uint8_t m;            // encode: m; decode: syndromes M
+  uint8_t n_pos;        // decode: codeword length n
+  uint8_t e;            // decode: outputs
+  uint8_t k;            // data blocks
+  uint8_t layout;       // kLayoutSymbol / kLayoutPacket
+  uint16_t pad;
+  uint32_t packet_bytes;  // packet layout: P
+  uint32_t pad2;
+};
+
+constexpr int kMaxPtrs = kMaxBlocks + kMaxM;
+constexpr int kMaxCoefWords = kMaxM * kMaxM * 16;
+
+struct JobParams {
+  const StripeDesc* stripes;  // device table, or nullptr for the inline stripe
+  const uint64_t* ptrs;       // device table, or nullptr
+  const uint32_t* coef;       // device table, or nullptr
+  int* status;                // device status word (0 = ok), may be nullptr
+  uint32_t n_stripes;
+  uint32_t total_tiles;
+  uint32_t slice_bytes;       // bytes of one block per tile
+  uint32_t depth;             // ring slots
+  // one stripe passed by value (single-stripe calls need no device tables)
+  StripeDesc inl_stripe;
+  uint64_t inl_ptrs[kMaxPtrs];
+  uint32_t inl_coef[kMaxCoefWords];
+};
+
+// Bytes of one warp segment (32 lanes x 32 symbols) in the symbol layout.
+RS_CHD constexpr uint32_t segment_bytes(int w) { return 32u * 32u * (uint32_t)(w / 8); }
+
+}  // namespace rsgb

@@ -1,0 +1,32 @@
+// Host-side launch interface between the C ABI and the kernel units.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "job.hpp"
+
+namespace rsgb {
+
+constexpr size_t kMaxDynamicSmem = 227u * 1024u;
+
+struct LaunchShape {
+  int grid = 0;        // CTAs
+  int threads = 0;     // (consumer warps + 1) * 32
+  size_t smem = 0;     // dynamic shared memory bytes
+};
+
+// Launch tuning knobs (chosen per code by the autotuner or the defaults).
+struct TuneCfg {
+  int consumer_warps = 8;  // NC
+  int depth = 16;          // ring slots
+  int ctas_per_sm = 1;
+};
+
+inline size_t ring_smem_bytes(uint32_t depth, uint32_t slice) {
+  return ((2u * depth * 8u + 127u) & ~127u) + (size_t)depth * slice;
+}
+
+cudaError_t launch_poly(int w, int M, int op, const JobParams& p, const LaunchShape& sh, cudaStream_t st);
+int poly_max_consumer_warps(int w, int M, int op);
+
+}  // namespace rsgb

@@ -1,0 +1,189 @@
+"""Python binding of the C ABI in include/rs_gb300.h (argument marshalling only).
+
+Every operation runs in the CUDA library librs_gb300.so; this module only
+turns torch tensors into device pointers and streams into handles.  It
+raises RuntimeError when the library has not been built: there is no CPU
+fallback.
+
+Functions keep the C names (rs_init, rs_encode, rs_decode, ...); the
+:class:`Code` class wraps a handle for convenience.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(PKG, "librs_gb300.so")
+
+RS_POLY, RS_VANDERMONDE, RS_CAUCHY = 0, 1, 2
+REALIZATIONS = {"poly": RS_POLY, "vandermonde": RS_VANDERMONDE, "cauchy": RS_CAUCHY}
+RS_READ_MIN, RS_READ_ALL = 0, 1
+STATUS = {0: "RS_OK", 1: "RS_EINVAL", 2: "RS_ETOOMANY_ERASURES", 3: "RS_ENOMEM", 4: "RS_ECUDA",
+          5: "RS_ETIMEOUT", 6: "RS_EUNSUPPORTED"}
+
+_lock = threading.Lock()
+_lib = None
+
+VP = ctypes.c_void_p
+
+
+class RSError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"{STATUS.get(status, status)}: {msg}")
+        self.status = status
+
+
+def lib() -> ctypes.CDLL:
+    """Load librs_gb300.so (raises if it was not built)."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            if not os.path.exists(LIB_PATH):
+                raise RuntimeError(f"{LIB_PATH} is missing: build it with "
+                                   "`python -m paper_1312_5155_gb300.build`")
+            L = ctypes.CDLL(LIB_PATH)
+            sig = {
+                "rs_version": (ctypes.c_int, []),
+                "rs_last_error": (ctypes.c_char_p, []),
+                "rs_init": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                                           ctypes.POINTER(VP)]),
+                "rs_destroy": (None, [VP]),
+                "rs_set_packet_bytes": (ctypes.c_int, [VP, ctypes.c_size_t]),
+                "rs_set_read_mode": (ctypes.c_int, [VP, ctypes.c_int]),
+                "rs_set_launch": (ctypes.c_int, [VP, ctypes.c_int, ctypes.c_int, ctypes.c_int]),
+                "rs_encode": (ctypes.c_int, [VP, ctypes.POINTER(VP), ctypes.POINTER(VP), ctypes.c_size_t, VP]),
+                "rs_decode": (ctypes.c_int, [VP, ctypes.POINTER(ctypes.c_int), ctypes.c_int,
+                                             ctypes.POINTER(VP), ctypes.c_size_t, VP]),
+                "rs_poll_status": (ctypes.c_int, [VP, ctypes.POINTER(ctypes.c_int)]),
+            }
+            for name, (res, args) in sig.items():
+                fn = getattr(L, name)
+                fn.restype = res
+                fn.argtypes = args
+            _lib = L
+    return _lib
+
+
+def _check(rc: int) -> None:
+    if rc != 0:
+        raise RSError(rc, lib().rs_last_error().decode())
+
+
+def _ptr(x) -> int:
+    if x is None:
+        return 0
+    if isinstance(x, int):
+        return x
+    return int(x.data_ptr())
+
+
+def _ptr_array(xs):
+    arr = (VP * len(xs))()
+    for i, x in enumerate(xs):
+        arr[i] = _ptr(x)
+    return arr
+
+
+def _stream(stream) -> int:
+    if stream is None:
+        import torch
+        return int(torch.cuda.current_stream().cuda_stream)
+    if isinstance(stream, int):
+        return stream
+    return int(stream.cuda_stream)
+
+
+# ------------------------------------------------------------ C-named API
+def rs_version() -> int:
+    return lib().rs_version()
+
+
+def rs_init(k: int, m: int, w: int, realization) -> int:
+    if isinstance(realization, str):
+        realization = REALIZATIONS[realization]
+    h = VP()
+    _check(lib().rs_init(k, m, w, realization, ctypes.byref(h)))
+    return h.value
+
+
+def rs_destroy(handle: int) -> None:
+    lib().rs_destroy(handle)
+
+
+def rs_set_packet_bytes(handle: int, packet_bytes: int) -> None:
+    _check(lib().rs_set_packet_bytes(handle, packet_bytes))
+
+
+def rs_set_read_mode(handle: int, mode: int) -> None:
+    _check(lib().rs_set_read_mode(handle, mode))
+
+
+def rs_set_launch(handle: int, consumer_warps: int = 0, depth: int = 0, ctas_per_sm: int = 0) -> None:
+    _check(lib().rs_set_launch(handle, consumer_warps, depth, ctas_per_sm))
+
+
+def rs_encode(handle: int, data, parity, block_bytes: int, stream=None) -> None:
+    _check(lib().rs_encode(handle, _ptr_array(data), _ptr_array(parity), block_bytes, _stream(stream)))
+
+
+def rs_decode(handle: int, erasures, blocks, block_bytes: int, stream=None) -> None:
+    er = (ctypes.c_int * max(1, len(erasures)))(*erasures)
+    _check(lib().rs_decode(handle, er, len(erasures), _ptr_array(blocks), block_bytes, _stream(stream)))
+
+
+def rs_poll_status(handle: int) -> int:
+    v = ctypes.c_int(0)
+    rc = lib().rs_poll_status(handle, ctypes.byref(v))
+    if rc not in (0, 5):
+        _check(rc)
+    return v.value
+
+
+# ---------------------------------------------------------------- wrapper
+class Code:
+    """RS(k, m) over GF(2^w) in one realization; owns its library handle."""
+
+    def __init__(self, k: int, m: int, w: int = 8, realization="poly", packet_bytes: int | None = None,
+                 read_mode: int = RS_READ_MIN):
+        self.k, self.m, self.w = k, m, w
+        self.realization = realization
+        self.handle = rs_init(k, m, w, realization)
+        if packet_bytes is not None:
+            rs_set_packet_bytes(self.handle, packet_bytes)
+        if read_mode != RS_READ_MIN:
+            rs_set_read_mode(self.handle, read_mode)
+
+    @property
+    def n(self) -> int:
+        return self.k + self.m
+
+    def set_launch(self, consumer_warps=0, depth=0, ctas_per_sm=0):
+        rs_set_launch(self.handle, consumer_warps, depth, ctas_per_sm)
+
+    def encode(self, data, parity, block_bytes: int | None = None, stream=None):
+        """data: k uint8 device tensors (or a (k, B) tensor); parity: m tensors / (m, B)."""
+        if block_bytes is None:
+            block_bytes = int(data[0].numel() * data[0].element_size())
+        rs_encode(self.handle, list(data), list(parity), block_bytes, stream)
+
+    def decode(self, erasures, blocks, block_bytes: int | None = None, stream=None):
+        """blocks: n uint8 device tensors (or an (n, B) tensor); erased ones are written."""
+        if block_bytes is None:
+            block_bytes = int(blocks[0].numel() * blocks[0].element_size())
+        rs_decode(self.handle, list(erasures), list(blocks), block_bytes, stream)
+
+    def poll_status(self) -> int:
+        return rs_poll_status(self.handle)
+
+    def close(self):
+        if getattr(self, "handle", None):
+            rs_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
