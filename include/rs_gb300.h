@@ -80,7 +80,8 @@ void rs_destroy(rs_code *code);
 /* Cauchy only: packet size P in bytes (§2.3 projection; default 2048).
  * A block is a sequence of super-packets of w*P bytes; packet c of a
  * super-packet holds bit c of its 8P symbols.  P must be a positive
- * multiple of 16; block_bytes must then be a multiple of w*P. */
+ * multiple of 128 (at most 1 MiB); block_bytes must then be a multiple of
+ * w*P. */
 rs_status rs_set_packet_bytes(rs_code *code, size_t packet_bytes);
 
 /* Which survivors a decode reads (rs_read_mode, default RS_READ_MIN). */
@@ -117,6 +118,59 @@ rs_status rs_decode(rs_code *code, const int *erasures, int n_erasures, void *co
  * *device_status receives 0 or the kernel's error code; the return value is
  * RS_ETIMEOUT when the word was set, RS_OK otherwise. */
 rs_status rs_poll_status(rs_code *code, int *device_status);
+
+/* ------------------------------------------------------------------------
+ * Batches: many stripe operations (any mix of codes, encodes and decodes of
+ * any block sizes) in one persistent launch per kernel group.  Tiles of all
+ * stripes are spread over one grid of (SMs x CTAs-per-SM) CTAs, so small
+ * blocks do not pay one launch each.
+ * ------------------------------------------------------------------------ */
+
+typedef enum { RS_OP_ENCODE = 0, RS_OP_DECODE = 1 } rs_op_kind;
+
+typedef struct {
+  rs_code *code;       /* code of this stripe (must outlive the batch's launches) */
+  int op;              /* rs_op_kind */
+  int n_erasures;      /* RS_OP_DECODE: number of erased blocks (0..m) */
+  int erasures[8];     /* RS_OP_DECODE: erased block indices in [0, n) */
+  void *blocks[64];    /* n = k + m device pointers: data blocks then parity
+                          blocks (same rules as rs_encode / rs_decode) */
+  size_t block_bytes;  /* bytes per block of this stripe */
+} rs_op;
+
+/* Create a batch able to hold up to max_ops operations (1..2^20).
+ * Allocates its device descriptor tables and a pinned staging buffer on
+ * the current device (about 4.7 KB per op).  Errors: RS_EINVAL, RS_ENOMEM,
+ * RS_ECUDA. */
+rs_status rs_batch_create(int max_ops, rs_batch **out);
+
+/* Free a batch (NULL is ignored); its launches must have completed. */
+void rs_batch_destroy(rs_batch *batch);
+
+/* Launch shape for the batch's kernels (as rs_set_launch). */
+rs_status rs_batch_set_launch(rs_batch *batch, int consumer_warps, int depth, int ctas_per_sm);
+
+/* Validate and plan n_ops operations (§3.2 / §3.3 / §2.1 per op, as in
+ * rs_encode / rs_decode), group them by kernel (at most 8 groups), and
+ * upload the descriptor tables asynchronously on `stream`.  Host-side
+ * errors name the failing op and leave the previous contents in place.
+ * Launch on the same stream (or synchronise) so the upload is ordered
+ * before the kernels.  A CUDA graph that captured rs_batch_launch stays
+ * valid after a later rs_batch_set as long as the new ops form the same
+ * kernel groups in the same order (rs_batch_kernel_count and the op mix
+ * unchanged): launch shapes are fixed and counts are read from device
+ * memory. */
+rs_status rs_batch_set(rs_batch *batch, const rs_op *ops, int n_ops, void *stream);
+
+/* Enqueue the batch's kernels on `stream` (one persistent launch per
+ * kernel group; no host synchronisation, no allocation). */
+rs_status rs_batch_launch(rs_batch *batch, void *stream);
+
+/* Number of kernel launches rs_batch_launch enqueues for the current set. */
+int rs_batch_kernel_count(const rs_batch *batch);
+
+/* Read and clear the batch's device status word (as rs_poll_status). */
+rs_status rs_batch_poll_status(rs_batch *batch, int *device_status);
 
 #ifdef __cplusplus
 }

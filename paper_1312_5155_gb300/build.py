@@ -29,8 +29,41 @@ ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC,-O2",
               "-I", CSRC, "-I", INCLUDE]
 
-# (w, M, op) instantiations of the polynomial kernel
-POLY_INSTANCES = [(w, m, op) for w in (8, 16) for m in range(1, 9) for op in (0, 1)]
+# Kernel instantiations: (name, body type, registry key fields).
+# Families: 0 poly, 1 matrix with runtime P, 2 matrix with compile-time P,
+# 3 mixed polynomial kernel.  ops: 0 poly encode, 1 poly decode,
+# 2 matrix encode, 3 matrix decode.  Layout: 0 symbol, 1 packet.
+# Kinds: 1 Vandermonde, 2 Cauchy.
+FIXED_CODES = [(8, 6, 3), (8, 10, 4), (8, 12, 4), (8, 20, 4), (16, 12, 4)]
+MIXED_POLY = [(8, (3, 4))]
+
+
+def instances():
+    out = []
+    for w in (8, 16):
+        for m in range(1, 9):
+            for op in (0, 1):
+                out.append((f"poly_w{w}_m{m}_op{op}", f"PolyBody<{w}, {m}, {op}>",
+                            dict(family=0, w=w, m=m, op=op)))
+    for w in (8, 16):
+        for m in range(1, 9):
+            for op in (2, 3):
+                for layout in (0, 1):
+                    out.append((f"matrt_w{w}_m{m}_op{op}_l{layout}", f"MatRuntimeBody<{w}, {m}, {op}, {layout}>",
+                                dict(family=1, w=w, m=m, op=op, layout=layout)))
+    for (w, k, m) in FIXED_CODES:
+        for kind in (1, 2):
+            for op in (2, 3):
+                layout = 1 if kind == 2 else 0
+                out.append((f"matfix_w{w}_k{k}_m{m}_kind{kind}_op{op}",
+                            f"MatFixedBody<{w}, {k}, {m}, {kind}, {op}>",
+                            dict(family=2, w=w, m=m, op=op, layout=layout, kind=kind, k=k)))
+    for (w, ms) in MIXED_POLY:
+        bodies = ", ".join(f"PolyBody<{w}, {m}, {op}>" for m in ms for op in (0, 1))
+        mset = sum(1 << m for m in ms)
+        out.append((f"polymix_w{w}_" + "_".join(map(str, ms)), f"MixedBody<{bodies}>",
+                    dict(family=3, w=w, m=0, op=-1, mset=mset)))
+    return out
 
 
 def nvcc() -> str:
@@ -57,21 +90,42 @@ def _write_if_changed(path: str, text: str) -> None:
 def generate_units() -> list[str]:
     os.makedirs(GEN, exist_ok=True)
     units = []
-    for w, m, op in POLY_INSTANCES:
-        path = os.path.join(GEN, f"poly_w{w}_m{m}_op{op}.cu")
+    insts = instances()
+    for name, body, _ in insts:
+        path = os.path.join(GEN, f"{name}.cu")
         _write_if_changed(path, (
             "// generated by paper_1312_5155_gb300/build.py\n"
             '#include "stripe_kernel.cuh"\n'
             "namespace rsgb {\n"
-            f"RSGB_DEFINE_POLY_LAUNCHER({w}, {m}, {op})\n"
-            "}\n"))
+            f"cudaError_t launch_{name}(const JobParams& p, const LaunchShape& sh, cudaStream_t st) {{\n"
+            f"  return launch_body<{body}>(p, sh, st);\n}}\n"
+            f"int warps_{name}() {{ return {body}::kMaxWarps; }}\n"
+            "}  // namespace rsgb\n"))
         units.append(path)
+    lines = ["// generated by paper_1312_5155_gb300/build.py", '#include "registry.hpp"', "namespace rsgb {"]
+    for name, _, _ in insts:
+        lines.append(f"cudaError_t launch_{name}(const JobParams&, const LaunchShape&, cudaStream_t);")
+        lines.append(f"int warps_{name}();")
+    lines.append("static const KernelEntry* build_table() {")
+    lines.append(f"  static KernelEntry t[{len(insts)}];")
+    for i, (name, _, key) in enumerate(insts):
+        k = dict(family=0, w=0, m=0, op=0, layout=0, kind=0, k=0, mset=0)
+        k.update(key)
+        lines.append(f"  t[{i}] = KernelEntry{{KernelKey{{{k['family']}, {k['w']}, {k['m']}, {k['op']}, "
+                     f"{k['layout']}, {k['kind']}, {k['k']}, {k['mset']}u}}, launch_{name}, warps_{name}(), "
+                     f'"{name}"}};')
+    lines.append("  return t;\n}")
+    lines.append("const KernelEntry* const kKernelRegistryPtr = build_table();")
+    lines.append(f"const int kKernelRegistrySize = {len(insts)};")
+    lines.append("}  // namespace rsgb")
+    reg = os.path.join(GEN, "registry.cu")
+    _write_if_changed(reg, "\n".join(lines) + "\n")
+    units.append(reg)
     return units
 
 
 def sources() -> list[str]:
-    return [os.path.join(CSRC, "capi.cu"), os.path.join(CSRC, "kernels_poly.cu"),
-            os.path.join(CSRC, "plan.cpp")] + generate_units()
+    return [os.path.join(CSRC, "capi.cu"), os.path.join(CSRC, "plan.cpp")] + generate_units()
 
 
 def _obj(src: str) -> str:

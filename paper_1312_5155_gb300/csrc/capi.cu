@@ -1,5 +1,6 @@
 // C ABI of the library (declared in include/rs_gb300.h): argument checks,
-// per-code generator construction, decode-plan cache and kernel launches.
+// per-code generator construction, decode-plan cache, single-stripe calls
+// and batches of stripe operations.
 #include <cuda_runtime.h>
 #include <stdint.h>
 #include <string.h>
@@ -13,6 +14,7 @@
 
 #include "launch.hpp"
 #include "plan.hpp"
+#include "registry.hpp"
 #include "rs_gb300.h"
 
 using namespace rsgb;
@@ -35,6 +37,21 @@ rs_status cuda_fail(cudaError_t e, const char* what) {
   return fail(RS_ECUDA, std::string(what) + ": " + cudaGetErrorString(e));
 }
 
+constexpr int kMaxGroups = 8;                        // kernels per batch launch
+constexpr int kKindOf[3] = {0, kKindVandermonde, kKindCauchy};
+
+bool has_fixed_kernels(int w, int k, int m) {
+  KernelKey key;
+  key.family = kFamMatFixed;
+  key.w = w;
+  key.m = m;
+  key.op = kOpMatEncode;
+  key.layout = 0;
+  key.kind = kKindVandermonde;
+  key.k = k;
+  return find_kernel(key) != nullptr;
+}
+
 }  // namespace
 
 struct rs_code {
@@ -43,7 +60,9 @@ struct rs_code {
   size_t packet_bytes = 2048;
   int read_mode = RS_READ_MIN;
   TuneCfg tune;
-  std::vector<uint32_t> P;  // parity rows of the generator (matrix realizations)
+  std::vector<uint32_t> P;       // parity rows of the generator (matrix realizations)
+  uint32_t* d_pmask = nullptr;   // column masks of P on the device (runtime-P kernels)
+  bool fixed = false;            // compile-time-P kernels exist for (w, k, m)
   int device = 0;
   int num_sms = 0;
   int* d_status = nullptr;
@@ -55,18 +74,17 @@ namespace {
 
 bool aligned16(const void* p) { return ((uintptr_t)p & 15u) == 0; }
 
-rs_status check_device(const rs_code* c) {
+rs_status check_device(int device) {
   int dev = -1;
   cudaError_t e = cudaGetDevice(&dev);
   if (e != cudaSuccess) return cuda_fail(e, "cudaGetDevice");
-  if (dev != c->device)
-    return fail(RS_EINVAL, "code was created on device " + std::to_string(c->device) +
-                               " but device " + std::to_string(dev) + " is current");
+  if (dev != device)
+    return fail(RS_EINVAL, "object was created on device " + std::to_string(device) + " but device " +
+                               std::to_string(dev) + " is current");
   return RS_OK;
 }
 
-// Blocks of one call must be pairwise disjoint (inputs are read while
-// outputs are written).
+// Blocks of one operation must be pairwise disjoint.
 bool disjoint(const std::vector<const void*>& ptrs, size_t bytes) {
   std::vector<uintptr_t> a;
   a.reserve(ptrs.size());
@@ -85,34 +103,12 @@ rs_status check_blocks(const rs_code* c, const std::vector<const void*>& ptrs, s
   if (c->w == 16 && (bytes & 1u)) return fail(RS_EINVAL, "block_bytes must be even for w = 16");
   if (c->real == Realization::Cauchy && bytes % ((size_t)c->w * c->packet_bytes))
     return fail(RS_EINVAL, "block_bytes must be a multiple of w * packet_bytes for the Cauchy realization");
-  if (!disjoint(ptrs, bytes)) return fail(RS_EINVAL, "blocks of one call must not overlap");
+  if (bytes > ((size_t)1 << 40)) return fail(RS_EINVAL, "block_bytes too large");
+  if (!disjoint(ptrs, bytes)) return fail(RS_EINVAL, "blocks of one operation must not overlap");
   return RS_OK;
 }
 
-void fill_masks(uint32_t* dst, const DecodePlan& pl, int w) {
-  const int M = pl.M;
-  for (int t = 0; t < M; ++t)
-    for (int j = 0; j < M; ++j)
-      for (int c = 0; c < w; ++c)
-        dst[(t * M + j) * w + c] = (t < pl.e && ((pl.W[t][j] >> c) & 1u)) ? 0xFFFFFFFFu : 0u;
-}
-
-// Shape of a launch over `total_tiles` tiles for a kernel with a consumer-warp cap.
-LaunchShape make_shape(const rs_code* c, int warp_cap, uint32_t total_tiles, uint32_t& slice,
-                       uint32_t& depth) {
-  const int nc = std::max(1, std::min(c->tune.consumer_warps, warp_cap));
-  slice = (uint32_t)nc * segment_bytes(c->w);
-  depth = (uint32_t)std::max(2, c->tune.depth);
-  while (depth > 2 && ring_smem_bytes(depth, slice) > kMaxDynamicSmem / (size_t)c->tune.ctas_per_sm) --depth;
-  LaunchShape sh;
-  sh.threads = (nc + 1) * 32;
-  sh.smem = ring_smem_bytes(depth, slice);
-  const uint32_t cap = (uint32_t)(c->num_sms * c->tune.ctas_per_sm);
-  sh.grid = (int)std::max<uint32_t>(1, std::min(total_tiles, cap));
-  return sh;
-}
-
-rs_status get_plan(rs_code* c, const int* er, int e, const DecodePlan** out) {
+rs_status get_plan(rs_code* c, const int* er, int e, DecodePlan& out) {
   std::vector<int> key;
   key.push_back(c->read_mode);
   key.insert(key.end(), er, er + e);
@@ -130,8 +126,229 @@ rs_status get_plan(rs_code* c, const int* er, int e, const DecodePlan** out) {
     if (c->plans.size() > 4096) c->plans.clear();
     it = c->plans.emplace(key, pl).first;
   }
-  *out = &it->second;
+  out = it->second;
   return RS_OK;
+}
+
+// One stripe operation, ready for a kernel: descriptor (tile_begin,
+// ptr_off, coef_off filled in by the launcher), pointers and masks.
+struct PreparedOp {
+  KernelKey key;
+  const KernelEntry* entry = nullptr;
+  StripeDesc d{};
+  std::vector<uint64_t> ptrs;
+  std::vector<uint32_t> coef;
+  bool noop = false;
+};
+
+rs_status select_kernel(const rs_code* c, int op, int M, PreparedOp& po) {
+  KernelKey key;
+  key.w = c->w;
+  key.m = M;
+  if (c->real == Realization::Poly) {
+    key.family = kFamPoly;
+    key.op = op;  // kOpEncode / kOpDecode
+  } else {
+    key.op = op == kOpEncode ? kOpMatEncode : kOpMatDecode;
+    key.layout = c->real == Realization::Cauchy ? kLayoutPacket : kLayoutSymbol;
+    if (c->fixed) {
+      key.family = kFamMatFixed;
+      key.kind = kKindOf[(int)c->real];
+      key.k = c->k;
+    } else {
+      key.family = kFamMatRuntime;
+    }
+  }
+  po.key = key;
+  po.entry = find_kernel(key);
+  if (!po.entry) return fail(RS_EUNSUPPORTED, "no kernel compiled for this code");
+  return RS_OK;
+}
+
+void fill_common(const rs_code* c, size_t B, StripeDesc& d) {
+  d.bytes = B;
+  d.k = (uint8_t)c->k;
+  d.layout = c->real == Realization::Cauchy ? kLayoutPacket : kLayoutSymbol;
+  d.packet_bytes = c->real == Realization::Cauchy ? (uint32_t)c->packet_bytes : 0u;
+  d.pmask = (uint64_t)(uintptr_t)c->d_pmask;
+}
+
+rs_status prepare_encode(rs_code* c, const void* const* data, void* const* parity, size_t B, PreparedOp& po) {
+  if (!data || !parity) return fail(RS_EINVAL, "pointer array is null");
+  std::vector<const void*> all;
+  for (int i = 0; i < c->k; ++i) all.push_back(data[i]);
+  for (int j = 0; j < c->m; ++j) all.push_back(parity[j]);
+  rs_status s = check_blocks(c, all, B);
+  if (s != RS_OK) return s;
+  if ((s = select_kernel(c, kOpEncode, c->m, po)) != RS_OK) return s;
+  po.noop = B == 0;
+  StripeDesc& d = po.d;
+  fill_common(c, B, d);
+  d.n_in = (uint16_t)c->k;
+  d.n_out = (uint16_t)c->m;
+  d.op = (uint8_t)po.key.op;
+  d.m = (uint8_t)c->m;
+  po.ptrs.clear();
+  if (c->real == Realization::Poly) {
+    // LFSR consumption order: d_{k-1} first (highest degree, §3.2 Eq. 2)
+    for (int i = c->k - 1; i >= 0; --i) po.ptrs.push_back((uint64_t)(uintptr_t)data[i]);
+  } else {
+    for (int i = 0; i < c->k; ++i) po.ptrs.push_back((uint64_t)(uintptr_t)data[i]);
+  }
+  for (int j = 0; j < c->m; ++j) po.ptrs.push_back((uint64_t)(uintptr_t)parity[j]);
+  po.coef.clear();
+  return RS_OK;
+}
+
+rs_status prepare_decode(rs_code* c, const int* er, int e, void* const* blocks, size_t B, PreparedOp& po) {
+  if (e < 0) return fail(RS_EINVAL, "negative erasure count");
+  if (e > c->m) return fail(RS_ETOOMANY_ERASURES, "more erasures than parity blocks");
+  if (e > 0 && !er) return fail(RS_EINVAL, "erasure list is null");
+  if (!blocks) return fail(RS_EINVAL, "pointer array is null");
+  const int n = c->k + c->m;
+  std::vector<const void*> all;
+  for (int b = 0; b < n; ++b) all.push_back(blocks[b]);
+  rs_status s = check_blocks(c, all, B);
+  if (s != RS_OK) return s;
+  DecodePlan pl;
+  if ((s = get_plan(c, er, e, pl)) != RS_OK) return s;
+  po.noop = e == 0 || B == 0;
+  if (e == 0) return RS_OK;
+  if ((s = select_kernel(c, kOpDecode, pl.M, po)) != RS_OK) return s;
+  StripeDesc& d = po.d;
+  fill_common(c, B, d);
+  d.read_mask = pl.read_mask;
+  d.n_in = (uint16_t)pl.in_blocks.size();
+  d.n_out = (uint16_t)pl.e;
+  d.op = (uint8_t)po.key.op;
+  d.m = (uint8_t)pl.M;
+  d.n_pos = (uint8_t)pl.n_pos;
+  d.e = (uint8_t)pl.e;
+  po.ptrs.clear();
+  for (int b : pl.in_blocks) po.ptrs.push_back((uint64_t)(uintptr_t)blocks[b]);
+  for (int b : pl.out_blocks) po.ptrs.push_back((uint64_t)(uintptr_t)blocks[b]);
+  const int M = pl.M;
+  po.coef.assign((size_t)M * M * c->w, 0u);
+  for (int t = 0; t < pl.e; ++t)
+    for (int j = 0; j < M; ++j)
+      for (int b = 0; b < c->w; ++b)
+        po.coef[(size_t)(t * M + j) * c->w + b] = ((pl.W[t][j] >> b) & 1u) ? 0xFFFFFFFFu : 0u;
+  return RS_OK;
+}
+
+// Consumer warps for a launch: the tuned value capped by the kernel; in
+// the packet layout a tile spans nc*128 bytes of a packet, which must
+// divide every packet size of the launch.
+int pick_warps(const TuneCfg& t, int cap, int layout, uint32_t packet_gcd) {
+  int nc = std::max(1, std::min(t.consumer_warps, cap));
+  if (layout == kLayoutPacket)
+    while (nc > 1 && packet_gcd % (uint32_t)(nc * 128)) --nc;
+  return nc;
+}
+
+LaunchShape make_shape(const TuneCfg& t, int nc, int w, int num_sms, uint32_t& slice, uint32_t& depth) {
+  slice = (uint32_t)nc * segment_bytes(w);
+  depth = (uint32_t)std::max(2, t.depth);
+  const size_t budget = kMaxDynamicSmem / (size_t)std::max(1, t.ctas_per_sm);
+  while (depth > 2 && ring_smem_bytes(depth, slice) > budget) --depth;
+  LaunchShape sh;
+  sh.threads = (nc + 1) * 32;
+  sh.smem = ring_smem_bytes(depth, slice);
+  sh.grid = std::max(1, num_sms * std::max(1, t.ctas_per_sm));
+  return sh;
+}
+
+uint32_t tiles_of(const StripeDesc& d, uint32_t slice) {
+  return (uint32_t)((d.bytes + slice - 1) / slice);
+}
+
+rs_status launch_single(rs_code* c, PreparedOp& po, void* stream) {
+  if (po.noop) return ok();
+  rs_status s = check_device(c->device);
+  if (s != RS_OK) return s;
+  JobParams* p = new (std::nothrow) JobParams();
+  if (!p) return fail(RS_ENOMEM, "host allocation failed");
+  const int nc = pick_warps(c->tune, po.entry->max_warps, po.key.layout, po.d.packet_bytes);
+  uint32_t slice, depth;
+  LaunchShape sh = make_shape(c->tune, nc, c->w, c->num_sms, slice, depth);
+  p->status = c->d_status;
+  p->n_stripes = 1;
+  p->slice_bytes = slice;
+  p->depth = depth;
+  p->inl_stripe = po.d;
+  p->inl_stripe.tile_begin = 0;
+  p->inl_stripe.ptr_off = 0;
+  p->inl_stripe.coef_off = 0;
+  p->total_tiles = tiles_of(po.d, slice);
+  sh.grid = (int)std::min<uint32_t>((uint32_t)sh.grid, p->total_tiles);
+  std::copy(po.ptrs.begin(), po.ptrs.end(), p->inl_ptrs);
+  std::copy(po.coef.begin(), po.coef.end(), p->inl_coef);
+  cudaError_t e = po.entry->launch(*p, sh, (cudaStream_t)stream);
+  delete p;
+  if (e != cudaSuccess) return cuda_fail(e, po.entry->name);
+  return ok();
+}
+
+}  // namespace
+
+// ------------------------------------------------------------------ batches
+struct rs_batch {
+  int max_ops = 0;
+  int device = 0;
+  int num_sms = 0;
+  TuneCfg tune;
+  StripeDesc* d_stripes = nullptr;  // kMaxGroups regions of max_ops
+  uint64_t* d_ptrs = nullptr;       // max_ops * kMaxPtrs
+  uint32_t* d_coef = nullptr;       // max_ops * kMaxCoefWords
+  uint32_t* d_counts = nullptr;     // kMaxGroups * 2
+  int* d_status = nullptr;
+  uint8_t* h_stage = nullptr;       // pinned upload staging
+  size_t stage_bytes = 0;
+  cudaEvent_t uploaded = nullptr;
+  bool upload_pending = false;
+  struct Group {
+    const KernelEntry* entry;
+    int layout;
+    int nc;
+    uint32_t slice, depth;
+    uint32_t n_stripes, tiles;
+    LaunchShape sh;
+  };
+  std::vector<Group> groups;
+};
+
+namespace {
+
+size_t stage_layout(int max_ops, size_t* off_ptrs, size_t* off_coef, size_t* off_counts) {
+  size_t o = sizeof(StripeDesc) * (size_t)kMaxGroups * max_ops;
+  *off_ptrs = o;
+  o += sizeof(uint64_t) * (size_t)max_ops * kMaxPtrs;
+  *off_coef = o;
+  o += sizeof(uint32_t) * (size_t)max_ops * kMaxCoefWords;
+  *off_counts = o;
+  o += sizeof(uint32_t) * kMaxGroups * 2;
+  return o;
+}
+
+void batch_free(rs_batch* b) {
+  if (b->d_stripes) cudaFree(b->d_stripes);
+  if (b->d_ptrs) cudaFree(b->d_ptrs);
+  if (b->d_coef) cudaFree(b->d_coef);
+  if (b->d_counts) cudaFree(b->d_counts);
+  if (b->d_status) cudaFree(b->d_status);
+  if (b->h_stage) cudaFreeHost(b->h_stage);
+  if (b->uploaded) cudaEventDestroy(b->uploaded);
+}
+
+// Kernel used for an op inside a batch: a mixed polynomial kernel replaces
+// per-M kernels when the batch holds several M it covers.
+const KernelEntry* mixed_for(const KernelKey& k) {
+  if (k.family != kFamPoly) return nullptr;
+  for (int i = 0; i < kKernelRegistrySize; ++i) {
+    const KernelEntry& e = kKernelRegistryPtr[i];
+    if (e.key.family == kFamPolyMixed && e.key.w == k.w && ((e.key.mset >> k.m) & 1u)) return &e;
+  }
+  return nullptr;
 }
 
 }  // namespace
@@ -165,12 +382,25 @@ rs_status rs_init(int k, int m, int w, int realization, rs_code** out) {
   } else if (c->real == Realization::Cauchy) {
     cauchy_parity_matrix(k, m, w, c->P);
   }
+  c->fixed = c->real != Realization::Poly && has_fixed_kernels(w, k, m);
   cudaError_t e = cudaGetDevice(&c->device);
   if (e == cudaSuccess) e = cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, c->device);
   if (e == cudaSuccess) e = cudaMalloc(&c->d_status, sizeof(int));
   if (e == cudaSuccess) e = cudaMemset(c->d_status, 0, sizeof(int));
+  if (e == cudaSuccess && c->real != Realization::Poly) {
+    // column masks [j][i][b] of P for the runtime-P kernels
+    std::vector<uint32_t> masks((size_t)k * m * w);
+    for (int j = 0; j < k; ++j)
+      for (int i = 0; i < m; ++i)
+        for (int b = 0; b < w; ++b)
+          masks[((size_t)j * m + i) * w + b] = ((c->P[(size_t)i * k + j] >> b) & 1u) ? 0xFFFFFFFFu : 0u;
+    e = cudaMalloc(&c->d_pmask, masks.size() * sizeof(uint32_t));
+    if (e == cudaSuccess)
+      e = cudaMemcpy(c->d_pmask, masks.data(), masks.size() * sizeof(uint32_t), cudaMemcpyHostToDevice);
+  }
   if (e != cudaSuccess) {
     if (c->d_status) cudaFree(c->d_status);
+    if (c->d_pmask) cudaFree(c->d_pmask);
     delete c;
     return cuda_fail(e, "rs_init");
   }
@@ -181,13 +411,15 @@ rs_status rs_init(int k, int m, int w, int realization, rs_code** out) {
 void rs_destroy(rs_code* c) {
   if (!c) return;
   if (c->d_status) cudaFree(c->d_status);
+  if (c->d_pmask) cudaFree(c->d_pmask);
   delete c;
 }
 
 rs_status rs_set_packet_bytes(rs_code* c, size_t packet_bytes) {
   if (!c) return fail(RS_EINVAL, "code is null");
   if (c->real != Realization::Cauchy) return fail(RS_EINVAL, "packet size applies to the Cauchy realization only");
-  if (packet_bytes == 0 || packet_bytes % 16) return fail(RS_EINVAL, "packet_bytes must be a positive multiple of 16");
+  if (packet_bytes == 0 || packet_bytes % 128 || packet_bytes > (1u << 20))
+    return fail(RS_EINVAL, "packet_bytes must be a positive multiple of 128 (at most 1 MiB)");
   c->packet_bytes = packet_bytes;
   return ok();
 }
@@ -199,112 +431,37 @@ rs_status rs_set_read_mode(rs_code* c, int mode) {
   return ok();
 }
 
-rs_status rs_set_launch(rs_code* c, int consumer_warps, int depth, int ctas_per_sm) {
-  if (!c) return fail(RS_EINVAL, "code is null");
+static rs_status set_tune(TuneCfg& t, int consumer_warps, int depth, int ctas_per_sm) {
   if (consumer_warps < 0 || consumer_warps > 16 || depth < 0 || depth > 64 || ctas_per_sm < 0 || ctas_per_sm > 4 ||
       (depth != 0 && depth < 2))
     return fail(RS_EINVAL, "launch shape out of range");
-  if (consumer_warps) c->tune.consumer_warps = consumer_warps;
-  if (depth) c->tune.depth = depth;
-  if (ctas_per_sm) c->tune.ctas_per_sm = ctas_per_sm;
+  if (consumer_warps) t.consumer_warps = consumer_warps;
+  if (depth) t.depth = depth;
+  if (ctas_per_sm) t.ctas_per_sm = ctas_per_sm;
   return ok();
+}
+
+rs_status rs_set_launch(rs_code* c, int consumer_warps, int depth, int ctas_per_sm) {
+  if (!c) return fail(RS_EINVAL, "code is null");
+  return set_tune(c->tune, consumer_warps, depth, ctas_per_sm);
 }
 
 rs_status rs_encode(rs_code* c, const void* const* data_ptrs, void* const* parity_ptrs, size_t block_bytes,
                     void* stream) {
   if (!c) return fail(RS_EINVAL, "code is null");
-  if (!data_ptrs || !parity_ptrs) return fail(RS_EINVAL, "pointer array is null");
-  std::vector<const void*> all;
-  for (int i = 0; i < c->k; ++i) all.push_back(data_ptrs[i]);
-  for (int j = 0; j < c->m; ++j) all.push_back(parity_ptrs[j]);
-  rs_status s = check_blocks(c, all, block_bytes);
+  PreparedOp po;
+  rs_status s = prepare_encode(c, data_ptrs, parity_ptrs, block_bytes, po);
   if (s != RS_OK) return s;
-  if ((s = check_device(c)) != RS_OK) return s;
-  if (block_bytes == 0) return ok();
-  if (c->real != Realization::Poly) return fail(RS_EUNSUPPORTED, "realization not available in this build");
-
-  JobParams* p = new (std::nothrow) JobParams();
-  if (!p) return fail(RS_ENOMEM, "host allocation failed");
-  uint32_t slice, depth;
-  const int cap = poly_max_consumer_warps(c->w, c->m, kOpEncode);
-  const int nc = std::max(1, std::min(c->tune.consumer_warps, cap));
-  const uint32_t seg = (uint32_t)nc * segment_bytes(c->w);
-  const uint32_t tiles = (uint32_t)((block_bytes + seg - 1) / seg);
-  LaunchShape sh = make_shape(c, cap, tiles, slice, depth);
-  p->status = c->d_status;
-  p->n_stripes = 1;
-  p->total_tiles = tiles;
-  p->slice_bytes = slice;
-  p->depth = depth;
-  StripeDesc& d = p->inl_stripe;
-  d.bytes = block_bytes;
-  d.tile_begin = 0;
-  d.ptr_off = 0;
-  d.n_in = (uint16_t)c->k;
-  d.n_out = (uint16_t)c->m;
-  d.op = kOpEncode;
-  d.m = (uint8_t)c->m;
-  d.k = (uint8_t)c->k;
-  d.layout = kLayoutSymbol;
-  for (int i = 0; i < c->k; ++i) p->inl_ptrs[i] = (uint64_t)(uintptr_t)data_ptrs[c->k - 1 - i];
-  for (int j = 0; j < c->m; ++j) p->inl_ptrs[c->k + j] = (uint64_t)(uintptr_t)parity_ptrs[j];
-  cudaError_t e = launch_poly(c->w, c->m, kOpEncode, *p, sh, (cudaStream_t)stream);
-  delete p;
-  if (e != cudaSuccess) return cuda_fail(e, "encode launch");
-  return ok();
+  return launch_single(c, po, stream);
 }
 
 rs_status rs_decode(rs_code* c, const int* erasures, int n_erasures, void* const* block_ptrs, size_t block_bytes,
                     void* stream) {
   if (!c) return fail(RS_EINVAL, "code is null");
-  if (n_erasures < 0) return fail(RS_EINVAL, "negative erasure count");
-  if (n_erasures > c->m) return fail(RS_ETOOMANY_ERASURES, "more erasures than parity blocks");
-  if (n_erasures > 0 && !erasures) return fail(RS_EINVAL, "erasure list is null");
-  if (!block_ptrs) return fail(RS_EINVAL, "pointer array is null");
-  const int n = c->k + c->m;
-  std::vector<const void*> all;
-  for (int b = 0; b < n; ++b) all.push_back(block_ptrs[b]);
-  rs_status s = check_blocks(c, all, block_bytes);
+  PreparedOp po;
+  rs_status s = prepare_decode(c, erasures, n_erasures, block_ptrs, block_bytes, po);
   if (s != RS_OK) return s;
-  if ((s = check_device(c)) != RS_OK) return s;
-  const DecodePlan* pl = nullptr;
-  if ((s = get_plan(c, erasures, n_erasures, &pl)) != RS_OK) return s;
-  if (n_erasures == 0 || block_bytes == 0) return ok();
-  if (c->real != Realization::Poly) return fail(RS_EUNSUPPORTED, "realization not available in this build");
-
-  JobParams* p = new (std::nothrow) JobParams();
-  if (!p) return fail(RS_ENOMEM, "host allocation failed");
-  uint32_t slice, depth;
-  const int cap = poly_max_consumer_warps(c->w, pl->M, kOpDecode);
-  const int nc = std::max(1, std::min(c->tune.consumer_warps, cap));
-  const uint32_t seg = (uint32_t)nc * segment_bytes(c->w);
-  const uint32_t tiles = (uint32_t)((block_bytes + seg - 1) / seg);
-  LaunchShape sh = make_shape(c, cap, tiles, slice, depth);
-  p->status = c->d_status;
-  p->n_stripes = 1;
-  p->total_tiles = tiles;
-  p->slice_bytes = slice;
-  p->depth = depth;
-  StripeDesc& d = p->inl_stripe;
-  d.bytes = block_bytes;
-  d.read_mask = pl->read_mask;
-  d.n_in = (uint16_t)pl->in_blocks.size();
-  d.n_out = (uint16_t)pl->e;
-  d.op = kOpDecode;
-  d.m = (uint8_t)pl->M;
-  d.n_pos = (uint8_t)pl->n_pos;
-  d.e = (uint8_t)pl->e;
-  d.k = (uint8_t)c->k;
-  d.layout = kLayoutSymbol;
-  d.coef_off = 0;
-  size_t q = 0;
-  for (int b : pl->in_blocks) p->inl_ptrs[q++] = (uint64_t)(uintptr_t)block_ptrs[b];
-  for (int b : pl->out_blocks) p->inl_ptrs[q++] = (uint64_t)(uintptr_t)block_ptrs[b];
-  fill_masks(p->inl_coef, *pl, c->w);
-  cudaError_t e = launch_poly(c->w, pl->M, kOpDecode, *p, sh, (cudaStream_t)stream);
-  delete p;
-  if (e != cudaSuccess) return cuda_fail(e, "decode launch");
-  return ok();
+  return launch_single(c, po, stream);
 }
 
 rs_status rs_poll_status(rs_code* c, int* device_status) {
@@ -315,6 +472,206 @@ rs_status rs_poll_status(rs_code* c, int* device_status) {
   if (v) {
     e = cudaMemset(c->d_status, 0, sizeof(int));
     if (e != cudaSuccess) return cuda_fail(e, "rs_poll_status");
+  }
+  if (device_status) *device_status = v;
+  return v ? fail(RS_ETIMEOUT, "device-side wait timed out (status " + std::to_string(v) + ")") : ok();
+}
+
+// ------------------------------------------------------------ batch API
+rs_status rs_batch_create(int max_ops, rs_batch** out) {
+  if (!out) return fail(RS_EINVAL, "out is null");
+  *out = nullptr;
+  if (max_ops < 1 || max_ops > (1 << 20)) return fail(RS_EINVAL, "max_ops must be in [1, 2^20]");
+  rs_batch* b = new (std::nothrow) rs_batch();
+  if (!b) return fail(RS_ENOMEM, "host allocation failed");
+  b->max_ops = max_ops;
+  size_t op, oc, ocn;
+  b->stage_bytes = stage_layout(max_ops, &op, &oc, &ocn);
+  cudaError_t e = cudaGetDevice(&b->device);
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&b->num_sms, cudaDevAttrMultiProcessorCount, b->device);
+  if (e == cudaSuccess) e = cudaMalloc(&b->d_stripes, sizeof(StripeDesc) * (size_t)kMaxGroups * max_ops);
+  if (e == cudaSuccess) e = cudaMalloc(&b->d_ptrs, sizeof(uint64_t) * (size_t)max_ops * kMaxPtrs);
+  if (e == cudaSuccess) e = cudaMalloc(&b->d_coef, sizeof(uint32_t) * (size_t)max_ops * kMaxCoefWords);
+  if (e == cudaSuccess) e = cudaMalloc(&b->d_counts, sizeof(uint32_t) * kMaxGroups * 2);
+  if (e == cudaSuccess) e = cudaMemset(b->d_counts, 0, sizeof(uint32_t) * kMaxGroups * 2);
+  if (e == cudaSuccess) e = cudaMalloc(&b->d_status, sizeof(int));
+  if (e == cudaSuccess) e = cudaMemset(b->d_status, 0, sizeof(int));
+  if (e == cudaSuccess) e = cudaMallocHost(&b->h_stage, b->stage_bytes);
+  if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->uploaded, cudaEventDisableTiming);
+  if (e != cudaSuccess) {
+    batch_free(b);
+    delete b;
+    return e == cudaErrorMemoryAllocation ? fail(RS_ENOMEM, "batch allocation failed") : cuda_fail(e, "rs_batch_create");
+  }
+  *out = b;
+  return ok();
+}
+
+void rs_batch_destroy(rs_batch* b) {
+  if (!b) return;
+  batch_free(b);
+  delete b;
+}
+
+rs_status rs_batch_set_launch(rs_batch* b, int consumer_warps, int depth, int ctas_per_sm) {
+  if (!b) return fail(RS_EINVAL, "batch is null");
+  return set_tune(b->tune, consumer_warps, depth, ctas_per_sm);
+}
+
+rs_status rs_batch_set(rs_batch* b, const rs_op* ops, int n_ops, void* stream) {
+  if (!b) return fail(RS_EINVAL, "batch is null");
+  if (n_ops < 0 || n_ops > b->max_ops) return fail(RS_EINVAL, "n_ops out of range");
+  if (n_ops > 0 && !ops) return fail(RS_EINVAL, "ops is null");
+  rs_status s = check_device(b->device);
+  if (s != RS_OK) return s;
+  // prepare every op
+  std::vector<PreparedOp> prep(n_ops);
+  for (int i = 0; i < n_ops; ++i) {
+    const rs_op& o = ops[i];
+    if (!o.code) return fail(RS_EINVAL, "op " + std::to_string(i) + ": code is null");
+    if (o.code->device != b->device) return fail(RS_EINVAL, "op " + std::to_string(i) + ": code on another device");
+    if (o.op == RS_OP_ENCODE)
+      s = prepare_encode(o.code, (const void* const*)o.blocks, (void* const*)(o.blocks + o.code->k), o.block_bytes,
+                         prep[i]);
+    else if (o.op == RS_OP_DECODE)
+      s = prepare_decode(o.code, o.erasures, o.n_erasures, o.blocks, o.block_bytes, prep[i]);
+    else
+      s = fail(RS_EINVAL, "unknown op kind");
+    if (s != RS_OK) return fail(s, "op " + std::to_string(i) + ": " + g_last_error);
+  }
+  // group by kernel (mixed polynomial kernels merge several M)
+  std::vector<const KernelEntry*> group_entry;
+  std::vector<std::vector<int>> members;
+  std::map<const KernelEntry*, int> primary_count;
+  for (auto& po : prep)
+    if (!po.noop) primary_count[po.entry]++;
+  std::map<const KernelEntry*, int> mixed_users;
+  for (auto& kv : primary_count) {
+    const KernelEntry* mx = mixed_for(kv.first->key);
+    if (mx) mixed_users[mx]++;
+  }
+  for (int i = 0; i < n_ops; ++i) {
+    if (prep[i].noop) continue;
+    const KernelEntry* e = prep[i].entry;
+    const KernelEntry* mx = mixed_for(e->key);
+    if (mx && mixed_users[mx] >= 2) e = mx;
+    int g = -1;
+    for (size_t j = 0; j < group_entry.size(); ++j)
+      if (group_entry[j] == e) g = (int)j;
+    if (g < 0) {
+      if ((int)group_entry.size() == kMaxGroups) return fail(RS_EUNSUPPORTED, "more than 8 kernel groups in one batch");
+      group_entry.push_back(e);
+      members.emplace_back();
+      g = (int)group_entry.size() - 1;
+    }
+    members[g].push_back(i);
+  }
+  // wait until the previous upload has left the staging buffer
+  if (b->upload_pending) {
+    cudaError_t e = cudaEventSynchronize(b->uploaded);
+    if (e != cudaSuccess) return cuda_fail(e, "rs_batch_set");
+    b->upload_pending = false;
+  }
+  size_t off_ptrs, off_coef, off_counts;
+  stage_layout(b->max_ops, &off_ptrs, &off_coef, &off_counts);
+  StripeDesc* hs = reinterpret_cast<StripeDesc*>(b->h_stage);
+  uint64_t* hp = reinterpret_cast<uint64_t*>(b->h_stage + off_ptrs);
+  uint32_t* hc = reinterpret_cast<uint32_t*>(b->h_stage + off_coef);
+  uint32_t* hn = reinterpret_cast<uint32_t*>(b->h_stage + off_counts);
+  memset(hn, 0, sizeof(uint32_t) * kMaxGroups * 2);
+  size_t np = 0, ncw = 0;
+  std::vector<rs_batch::Group> groups;
+  for (size_t g = 0; g < group_entry.size(); ++g) {
+    rs_batch::Group gr{};
+    gr.entry = group_entry[g];
+    const int layout = prep[members[g][0]].key.layout;
+    uint32_t pg = 0;
+    for (int i : members[g]) {
+      const uint32_t pb = prep[i].d.packet_bytes;
+      uint32_t a = pg, c2 = pb;
+      while (c2) { uint32_t t = a % c2; a = c2; c2 = t; }
+      pg = a;
+    }
+    gr.layout = layout;
+    gr.nc = pick_warps(b->tune, gr.entry->max_warps, layout, pg);
+    const int w = gr.entry->key.w;
+    gr.sh = make_shape(b->tune, gr.nc, w, b->num_sms, gr.slice, gr.depth);
+    uint32_t tiles = 0;
+    StripeDesc* region = hs + g * (size_t)b->max_ops;
+    for (size_t q = 0; q < members[g].size(); ++q) {
+      PreparedOp& po = prep[members[g][q]];
+      StripeDesc d = po.d;
+      d.tile_begin = tiles;
+      d.ptr_off = (uint32_t)np;
+      d.coef_off = (uint32_t)ncw;
+      tiles += tiles_of(d, gr.slice);
+      std::copy(po.ptrs.begin(), po.ptrs.end(), hp + np);
+      np += po.ptrs.size();
+      std::copy(po.coef.begin(), po.coef.end(), hc + ncw);
+      ncw += po.coef.size();
+      region[q] = d;
+    }
+    gr.n_stripes = (uint32_t)members[g].size();
+    gr.tiles = tiles;
+    hn[2 * g] = gr.n_stripes;
+    hn[2 * g + 1] = tiles;
+    groups.push_back(gr);
+  }
+  // upload (stream-ordered)
+  cudaStream_t st = (cudaStream_t)stream;
+  cudaError_t e = cudaSuccess;
+  for (size_t g = 0; g < groups.size() && e == cudaSuccess; ++g)
+    e = cudaMemcpyAsync(b->d_stripes + g * (size_t)b->max_ops, hs + g * (size_t)b->max_ops,
+                        sizeof(StripeDesc) * groups[g].n_stripes, cudaMemcpyHostToDevice, st);
+  if (e == cudaSuccess && np) e = cudaMemcpyAsync(b->d_ptrs, hp, sizeof(uint64_t) * np, cudaMemcpyHostToDevice, st);
+  if (e == cudaSuccess && ncw)
+    e = cudaMemcpyAsync(b->d_coef, hc, sizeof(uint32_t) * ncw, cudaMemcpyHostToDevice, st);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(b->d_counts, hn, sizeof(uint32_t) * kMaxGroups * 2, cudaMemcpyHostToDevice, st);
+  if (e == cudaSuccess) e = cudaEventRecord(b->uploaded, st);
+  if (e != cudaSuccess) return cuda_fail(e, "rs_batch_set upload");
+  b->upload_pending = true;
+  b->groups = groups;
+  return ok();
+}
+
+rs_status rs_batch_launch(rs_batch* b, void* stream) {
+  if (!b) return fail(RS_EINVAL, "batch is null");
+  rs_status s = check_device(b->device);
+  if (s != RS_OK) return s;
+  JobParams* p = new (std::nothrow) JobParams();
+  if (!p) return fail(RS_ENOMEM, "host allocation failed");
+  for (size_t g = 0; g < b->groups.size(); ++g) {
+    const rs_batch::Group& gr = b->groups[g];
+    p->stripes = b->d_stripes + g * (size_t)b->max_ops;
+    p->ptrs = b->d_ptrs;
+    p->coef = b->d_coef;
+    p->counts = b->d_counts + 2 * g;
+    p->status = b->d_status;
+    p->n_stripes = gr.n_stripes;
+    p->total_tiles = gr.tiles;
+    p->slice_bytes = gr.slice;
+    p->depth = gr.depth;
+    cudaError_t e = gr.entry->launch(*p, gr.sh, (cudaStream_t)stream);
+    if (e != cudaSuccess) {
+      delete p;
+      return cuda_fail(e, gr.entry->name);
+    }
+  }
+  delete p;
+  return ok();
+}
+
+int rs_batch_kernel_count(const rs_batch* b) { return b ? (int)b->groups.size() : 0; }
+
+rs_status rs_batch_poll_status(rs_batch* b, int* device_status) {
+  if (!b) return fail(RS_EINVAL, "batch is null");
+  int v = 0;
+  cudaError_t e = cudaMemcpy(&v, b->d_status, sizeof(int), cudaMemcpyDeviceToHost);
+  if (e != cudaSuccess) return cuda_fail(e, "rs_batch_poll_status");
+  if (v) {
+    e = cudaMemset(b->d_status, 0, sizeof(int));
+    if (e != cudaSuccess) return cuda_fail(e, "rs_batch_poll_status");
   }
   if (device_status) *device_status = v;
   return v ? fail(RS_ETIMEOUT, "device-side wait timed out (status " + std::to_string(v) + ")") : ok();

@@ -22,6 +22,9 @@ enum : uint8_t {
 
 enum : uint8_t { kLayoutSymbol = 0, kLayoutPacket = 1 };
 
+// Matrix realizations with a compile-time generator
+enum : int { kKindVandermonde = 1, kKindCauchy = 2 };
+
 struct StripeDesc {
   uint64_t bytes;       // block bytes B
   uint64_t read_mask;   // decode: bit p set = position / block p is read
@@ -39,6 +42,8 @@ struct StripeDesc {
   uint16_t pad;
   uint32_t packet_bytes;  // packet layout: P
   uint32_t pad2;
+  uint64_t pmask;       // matrix realizations, runtime P: device table of
+                        // column masks [j][i][c] (k x m x W words)
 };
 
 constexpr int kMaxPtrs = kMaxBlocks + kMaxM;
@@ -49,6 +54,7 @@ struct JobParams {
   const uint64_t* ptrs;       // device table, or nullptr
   const uint32_t* coef;       // device table, or nullptr
   int* status;                // device status word (0 = ok), may be nullptr
+  const uint32_t* counts;     // device {n_stripes, total_tiles}, or nullptr
   uint32_t n_stripes;
   uint32_t total_tiles;
   uint32_t slice_bytes;       // bytes of one block per tile

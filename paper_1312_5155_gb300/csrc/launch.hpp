@@ -26,7 +26,5 @@ inline size_t ring_smem_bytes(uint32_t depth, uint32_t slice) {
   return ((2u * depth * 8u + 127u) & ~127u) + (size_t)depth * slice;
 }
 
-cudaError_t launch_poly(int w, int M, int op, const JobParams& p, const LaunchShape& sh, cudaStream_t st);
-int poly_max_consumer_warps(int w, int M, int op);
 
 }  // namespace rsgb

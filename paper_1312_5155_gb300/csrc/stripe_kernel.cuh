@@ -1,36 +1,41 @@
 // Persistent, TMA-staged stripe kernel (sm_103a).
 //
 // CTA = NC consumer warps + 1 producer warp.  The producer's lane 0 walks the
-// CTA's tiles (global tile t = blockIdx.x + i * gridDim.x) and, for every
-// input block of the tile's stripe, issues one 1-D bulk copy of the tile's
-// slice of that block into the next ring slot (full barrier counts the
-// bytes).  Consumer warps walk the same tile sequence; each thread owns 32
-// symbol columns of its warp's segment of the slice, loads them from the
-// slot (16-byte LDS per chunk), runs the codec on bit-planes in registers
-// and stores the output chunks straight to global memory.  Slots are
-// released through the empty barriers (every consumer thread arrives).
+// CTA's tiles (global tile t = blockIdx.x + i * gridDim.x over all stripes of
+// the launch) and, for every input block of the tile's stripe, issues 1-D
+// bulk copies (cp.async.bulk) of the tile's slice of that block into the
+// next slot of a shared-memory ring; the slot's full mbarrier counts the
+// bytes.  Consumer warps walk the same tile sequence; every thread owns 32
+// columns of the tile, reads them from the slot, runs the codec ("body") on
+// bit-planes in registers and stores its output words straight to global
+// memory.  Slots go back to the producer through the empty mbarriers (every
+// consumer thread arrives once per slot use).
 //
-// Symbol layout: warp segment = 32 lanes x 32 symbols; lane l owns the
-// 16-byte chunks at l*16 + c*512 (c < W/4) of the segment, so each warp-wide
-// load or store instruction covers 512 contiguous bytes.
+// Layouts
+//   symbol: columns are bytes (w = 8) or little-endian 16-bit words
+//     (w = 16).  Warp segment = 32 lanes x 32 symbols; lane l owns the
+//     16-byte chunks at l*16 + c*512 (c < W/4) of its segment, so every
+//     warp-wide load/store covers 512 contiguous bytes.  Slice of one block
+//     per tile = NC segments, one bulk copy.
+//   packet (§2.3 bit-matrix layout): a block is super-packets of W packets of
+//     P bytes; packet c holds bit c of the super-packet's 8P symbols.  A tile
+//     covers a span of NC*128 bytes at the same offset of the W packets of one
+//     super-packet (W bulk copies per block); lane l of warp v owns 32-bit
+//     word v*32 + l of the span in each packet, which are already the W
+//     bit-planes of 32 symbols.
 #pragma once
 #include <cuda_runtime.h>
 
 #include <mutex>
+#include <type_traits>
 
+#include "codec_matrix.hpp"
 #include "codec_poly.hpp"
 #include "job.hpp"
 #include "launch.hpp"
 #include "pipeline.cuh"
 
 namespace rsgb {
-
-// Thread cap per instantiation: small register footprints get up to 16
-// consumer warps, large ones (decode, or big M*W) up to 8.
-RS_CHD constexpr int max_consumer_warps(int w, int m, int op) {
-  return (op == kOpEncode && m * w <= 64) ? 16 : 8;
-}
-RS_CHD constexpr int max_threads(int w, int m, int op) { return (max_consumer_warps(w, m, op) + 1) * 32; }
 
 struct Ring {
   uint64_t* full;
@@ -58,7 +63,41 @@ __device__ __forceinline__ uint32_t find_stripe(const StripeDesc* st, uint32_t n
   return lo;
 }
 
-// Consumer-side view of one tile in the symbol layout.
+// Where tile `lt` of a stripe lies: symbol layout -> one byte range
+// [goff, goff + len) of every block; packet layout -> super-packet `sp_off`,
+// byte `span_off` inside each packet (len = span).
+struct TileGeom {
+  uint64_t goff;
+  uint32_t len;
+  uint32_t span_off;
+};
+
+__device__ __forceinline__ TileGeom tile_geom(const StripeDesc& d, uint32_t lt, uint32_t slice, int w) {
+  TileGeom g;
+  if (d.layout == kLayoutSymbol) {
+    g.goff = (uint64_t)lt * slice;
+    const uint64_t rem = d.bytes - g.goff;
+    g.len = rem < slice ? (uint32_t)rem : slice;
+    g.span_off = 0;
+  } else {
+    const uint32_t span = slice / (uint32_t)w;
+    const uint32_t per_sp = d.packet_bytes / span;
+    const uint32_t sp = lt / per_sp;
+    g.goff = (uint64_t)sp * (uint64_t)w * d.packet_bytes;
+    g.span_off = (lt - sp * per_sp) * span;
+    g.len = span;
+  }
+  return g;
+}
+
+__device__ __forceinline__ void wait_or_fail(uint64_t* bar, uint32_t par, bool& failed, int* status, int code) {
+  if (!failed && !mbar_wait(bar, par)) {
+    failed = true;
+    record_status(status, code);
+  }
+}
+
+// ------------------------------------------------------ consumer tile views
 template <int W>
 struct SymTile {
   Ring* ring;
@@ -71,14 +110,18 @@ struct SymTile {
   int* status;
   bool failed;
 
+  __device__ __forceinline__ void begin(const StripeDesc& d, const TileGeom& g, const uint64_t* p) {
+    ptrs = p;
+    n_in = d.n_in;
+    goff = g.goff;
+    len = g.len;
+  }
+
   __device__ __forceinline__ void load(int i, uint32_t* x) {
     Ring& r = *ring;
     const uint32_t s = r.s, par = r.par;
     r.advance();
-    if (!failed && !mbar_wait(&r.full[s], par)) {
-      failed = true;
-      record_status(status, kDevErrTimeoutFull);
-    }
+    wait_or_fail(&r.full[s], par, failed, status, kDevErrTimeoutFull);
     const uint8_t* slot = r.slots + (size_t)s * r.slice;
     const uint32_t len16 = len & ~15u;
 #pragma unroll
@@ -125,25 +168,148 @@ struct SymTile {
   }
 };
 
+template <int W>
+struct PacketTile {
+  Ring* ring;
+  const uint64_t* ptrs;
+  int n_in;
+  uint64_t goff;      // super-packet offset
+  uint32_t span_off;  // offset inside each packet
+  uint32_t span;      // bytes per packet row in the slot
+  uint32_t P;         // packet bytes
+  uint32_t word;      // this thread's 32-bit word inside the span
+  int* status;
+  bool failed;
+
+  __device__ __forceinline__ void begin(const StripeDesc& d, const TileGeom& g, const uint64_t* p) {
+    ptrs = p;
+    n_in = d.n_in;
+    goff = g.goff;
+    span_off = g.span_off;
+    P = d.packet_bytes;
+  }
+
+  __device__ __forceinline__ void load(int i, uint32_t* x) {
+    Ring& r = *ring;
+    const uint32_t s = r.s, par = r.par;
+    r.advance();
+    wait_or_fail(&r.full[s], par, failed, status, kDevErrTimeoutFull);
+    const uint8_t* slot = r.slots + (size_t)s * r.slice;
+#pragma unroll
+    for (int c = 0; c < W; ++c)
+      x[c] = failed ? 0u : *reinterpret_cast<const uint32_t*>(slot + (size_t)c * span + 4u * word);
+    mbar_arrive(&r.empty[s]);
+  }
+
+  __device__ __forceinline__ void store(int t, const uint32_t* x) {
+    if (failed) return;
+    uint8_t* out = reinterpret_cast<uint8_t*>(ptrs[n_in + t]) + goff + span_off + 4u * word;
+#pragma unroll
+    for (int c = 0; c < W; ++c) *reinterpret_cast<uint32_t*>(out + (size_t)c * P) = x[c];
+  }
+};
+
 // Runtime matrix W[t][j] as masks, layout [t][j][c] with dims M x M x W.
 template <int W, int M>
 struct CoefMasks {
   const uint32_t* base;
-  __device__ __forceinline__ uint32_t mask(int t, int j, int c) const {
-    return base[(t * M + j) * W + c];
+  __device__ __forceinline__ uint32_t mask(int t, int j, int c) const { return base[(t * M + j) * W + c]; }
+};
+
+// Runtime parity matrix P as masks, layout [j][i][c] with dims k x m x W.
+template <int W, int M>
+struct ColumnMasks {
+  const uint32_t* base;
+  __device__ __forceinline__ uint32_t mask(int j, int i, int c) const { return base[(j * M + i) * W + c]; }
+};
+
+// ------------------------------------------------------------------ bodies
+RS_CHD constexpr int body_warps(int regs_words) { return regs_words <= 64 ? 16 : 8; }
+
+template <int W, int M, int OP>
+struct PolyBody {
+  static constexpr int kW = W;
+  static constexpr int kLayout = kLayoutSymbol;
+  static constexpr int kMaxWarps = OP == kOpEncode ? body_warps(M * W) : 8;
+  __device__ static bool matches(const StripeDesc& d) { return d.op == OP && d.m == M; }
+  template <class Tile>
+  __device__ static void run(const StripeDesc& d, Tile& t, const uint32_t* coef) {
+    if constexpr (OP == kOpEncode) {
+      PolyEncode<W, M>::run((int)d.k, t, t);
+    } else {
+      CoefMasks<W, M> cm{coef + d.coef_off};
+      PolyDecode<W, M>::run((int)d.n_pos, d.read_mask, (int)d.e, t, t, cm);
+    }
   }
 };
 
-__device__ __forceinline__ void producer_loop(const JobParams& p, const StripeDesc* stripes,
-                                              const uint64_t* ptrs, Ring& ring) {
+template <int W, int M, int OP, int LAYOUT>
+struct MatRuntimeBody {
+  static constexpr int kW = W;
+  static constexpr int kLayout = LAYOUT;
+  static constexpr int kMaxWarps = 8;
+  __device__ static bool matches(const StripeDesc& d) { return d.op == OP && d.m == M; }
+  template <class Tile>
+  __device__ static void run(const StripeDesc& d, Tile& t, const uint32_t* coef) {
+    ColumnMasks<W, M> cols{reinterpret_cast<const uint32_t*>(d.pmask)};
+    if constexpr (OP == kOpMatEncode) {
+      MatEncodeRuntime<W, M, LAYOUT == kLayoutSymbol>::run((int)d.k, t, t, cols);
+    } else {
+      CoefMasks<W, M> cm{coef + d.coef_off};
+      MatDecodeRuntime<W, M, LAYOUT == kLayoutSymbol>::run((int)d.k, d.read_mask, (int)d.e, t, t, cols, cm);
+    }
+  }
+};
+
+template <int W, int K, int M, int KIND, int OP>
+struct MatFixedBody {
+  static constexpr int kW = W;
+  static constexpr int kLayout = KIND == kKindCauchy ? kLayoutPacket : kLayoutSymbol;
+  static constexpr int kMaxWarps = 8;
+  __device__ static bool matches(const StripeDesc& d) { return d.op == OP && d.m == M && d.k == K; }
+  template <class Tile>
+  __device__ static void run(const StripeDesc& d, Tile& t, const uint32_t* coef) {
+    if constexpr (OP == kOpMatEncode) {
+      MatEncodeFixed<W, K, M, KIND, kLayout == kLayoutSymbol>::run(t, t);
+    } else {
+      CoefMasks<W, M> cm{coef + d.coef_off};
+      MatDecodeFixed<W, K, M, KIND, kLayout == kLayoutSymbol>::run(d.read_mask, (int)d.e, t, t, cm);
+    }
+  }
+};
+
+// Several bodies of the same width and layout in one kernel: each stripe
+// runs the first body whose matches() accepts it.
+template <class First, class... Rest>
+struct MixedBody {
+  static constexpr int kW = First::kW;
+  static constexpr int kLayout = First::kLayout;
+  static constexpr int min_warps() {
+    int w = First::kMaxWarps;
+    ((w = Rest::kMaxWarps < w ? Rest::kMaxWarps : w), ...);
+    return w;
+  }
+  static constexpr int kMaxWarps = min_warps();
+  __device__ static bool matches(const StripeDesc& d) { return First::matches(d) || (Rest::matches(d) || ...); }
+  template <class Tile>
+  __device__ static void run(const StripeDesc& d, Tile& t, const uint32_t* coef) {
+    if (First::matches(d)) {
+      First::run(d, t, coef);
+      return;
+    }
+    if constexpr (sizeof...(Rest) > 0) MixedBody<Rest...>::run(d, t, coef);
+  }
+};
+
+// ---------------------------------------------------------------- producer
+template <int W, int LAYOUT>
+__device__ __forceinline__ void producer_loop(const JobParams& p, const StripeDesc* stripes, const uint64_t* ptrs,
+                                              Ring& ring, uint32_t n_stripes, uint32_t total_tiles) {
   uint32_t q = 0;
   bool ok = true;
-  for (uint32_t tile = blockIdx.x; tile < p.total_tiles && ok; tile += gridDim.x) {
-    const StripeDesc& d = stripes[find_stripe(stripes, p.n_stripes, tile)];
-    const uint64_t goff = (uint64_t)(tile - d.tile_begin) * ring.slice;
-    const uint64_t rem = d.bytes - goff;
-    const uint32_t len = rem < ring.slice ? (uint32_t)rem : ring.slice;
-    const uint32_t len16 = len & ~15u;
+  for (uint32_t tile = blockIdx.x; tile < total_tiles && ok; tile += gridDim.x) {
+    const StripeDesc& d = stripes[find_stripe(stripes, n_stripes, tile)];
+    const TileGeom g = tile_geom(d, tile - d.tile_begin, ring.slice, W);
     const uint64_t* ip = ptrs + d.ptr_off;
     for (int i = 0; i < d.n_in; ++i) {
       const uint32_t s = ring.s, par = ring.par;
@@ -153,11 +319,20 @@ __device__ __forceinline__ void producer_loop(const JobParams& p, const StripeDe
         break;
       }
       uint8_t* dst = ring.slots + (size_t)s * ring.slice;
-      if (len16) {
-        mbar_arrive_expect_tx(&ring.full[s], len16);
-        tma_load_1d(dst, reinterpret_cast<const uint8_t*>(ip[i]) + goff, len16, &ring.full[s]);
+      const uint8_t* src = reinterpret_cast<const uint8_t*>(ip[i]) + g.goff;
+      if constexpr (LAYOUT == kLayoutSymbol) {
+        const uint32_t len16 = g.len & ~15u;
+        if (len16) {
+          mbar_arrive_expect_tx(&ring.full[s], len16);
+          tma_load_1d(dst, src, len16, &ring.full[s]);
+        } else {
+          mbar_arrive(&ring.full[s]);
+        }
       } else {
-        mbar_arrive(&ring.full[s]);
+        const uint32_t span = ring.slice / (uint32_t)W;
+        mbar_arrive_expect_tx(&ring.full[s], ring.slice);
+        for (int c = 0; c < W; ++c)
+          tma_load_1d(dst + (size_t)c * span, src + (size_t)c * d.packet_bytes + g.span_off, span, &ring.full[s]);
       }
       ring.advance();
       ++q;
@@ -174,8 +349,11 @@ __device__ __forceinline__ void producer_loop(const JobParams& p, const StripeDe
   }
 }
 
-template <int W, int M, int OP>
-__global__ void __launch_bounds__(max_threads(W, M, OP), 1) rs_poly_kernel(const __grid_constant__ JobParams p) {
+// ------------------------------------------------------------------ kernel
+template <class Body>
+__global__ void __launch_bounds__((Body::kMaxWarps + 1) * 32, 1)
+    rs_stripe_kernel(const __grid_constant__ JobParams p) {
+  constexpr int W = Body::kW;
   extern __shared__ __align__(128) uint8_t smem[];
   const uint32_t depth = p.depth;
   Ring ring;
@@ -197,38 +375,38 @@ __global__ void __launch_bounds__(max_threads(W, M, OP), 1) rs_poly_kernel(const
   const StripeDesc* stripes = p.stripes ? p.stripes : &p.inl_stripe;
   const uint64_t* ptrs = p.ptrs ? p.ptrs : p.inl_ptrs;
   const uint32_t* coef = p.coef ? p.coef : p.inl_coef;
+  const uint32_t n_stripes = p.counts ? p.counts[0] : p.n_stripes;
+  const uint32_t total_tiles = p.counts ? p.counts[1] : p.total_tiles;
 
   if (warp == nc) {
-    if (lane == 0) producer_loop(p, stripes, ptrs, ring);
+    if (lane == 0) producer_loop<W, Body::kLayout>(p, stripes, ptrs, ring, n_stripes, total_tiles);
     return;
   }
 
-  SymTile<W> tile;
+  using Tile = std::conditional_t<Body::kLayout == kLayoutSymbol, SymTile<W>, PacketTile<W>>;
+  Tile tile;
   tile.ring = &ring;
-  tile.lane = (uint32_t)lane;
-  tile.seg = (uint32_t)warp * segment_bytes(W);
   tile.status = p.status;
   tile.failed = false;
-  for (uint32_t t = blockIdx.x; t < p.total_tiles; t += gridDim.x) {
-    const StripeDesc& d = stripes[find_stripe(stripes, p.n_stripes, t)];
-    tile.goff = (uint64_t)(t - d.tile_begin) * ring.slice;
-    const uint64_t rem = d.bytes - tile.goff;
-    tile.len = rem < ring.slice ? (uint32_t)rem : ring.slice;
-    tile.ptrs = ptrs + d.ptr_off;
-    tile.n_in = d.n_in;
-    if constexpr (OP == kOpEncode) {
-      PolyEncode<W, M>::run((int)d.k, tile, tile);
-    } else {
-      CoefMasks<W, M> cm{coef + d.coef_off};
-      PolyDecode<W, M>::run((int)d.n_pos, d.read_mask, (int)d.e, tile, tile, cm);
-    }
+  if constexpr (Body::kLayout == kLayoutSymbol) {
+    tile.lane = (uint32_t)lane;
+    tile.seg = (uint32_t)warp * segment_bytes(W);
+  } else {
+    tile.word = (uint32_t)(warp * 32 + lane);
+    tile.span = ring.slice / (uint32_t)W;
+  }
+  for (uint32_t t = blockIdx.x; t < total_tiles; t += gridDim.x) {
+    const StripeDesc& d = stripes[find_stripe(stripes, n_stripes, t)];
+    const TileGeom g = tile_geom(d, t - d.tile_begin, ring.slice, W);
+    tile.begin(d, g, ptrs + d.ptr_off);
+    Body::run(d, tile, coef);
     if (tile.failed) break;
   }
 }
 
 // Launch one instantiation (sets the shared-memory attribute once per device).
-template <int W, int M, int OP>
-cudaError_t launch_poly_instance(const JobParams& p, const LaunchShape& sh, cudaStream_t st) {
+template <class Body>
+cudaError_t launch_body(const JobParams& p, const LaunchShape& sh, cudaStream_t st) {
   constexpr int kMaxDevices = 64;
   static std::once_flag once[kMaxDevices];
   static cudaError_t attr_err[kMaxDevices];
@@ -236,21 +414,14 @@ cudaError_t launch_poly_instance(const JobParams& p, const LaunchShape& sh, cuda
   cudaError_t e = cudaGetDevice(&dev);
   if (e != cudaSuccess) return e;
   if (dev < 0 || dev >= kMaxDevices) return cudaErrorInvalidDevice;
-  if (sh.threads > max_threads(W, M, OP)) return cudaErrorInvalidConfiguration;
+  if (sh.threads > (Body::kMaxWarps + 1) * 32) return cudaErrorInvalidConfiguration;
   std::call_once(once[dev], [&] {
-    attr_err[dev] = cudaFuncSetAttribute(rs_poly_kernel<W, M, OP>,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kMaxDynamicSmem);
+    attr_err[dev] = cudaFuncSetAttribute(rs_stripe_kernel<Body>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)kMaxDynamicSmem);
   });
   if (attr_err[dev] != cudaSuccess) return attr_err[dev];
-  rs_poly_kernel<W, M, OP><<<sh.grid, sh.threads, sh.smem, st>>>(p);
+  rs_stripe_kernel<Body><<<sh.grid, sh.threads, sh.smem, st>>>(p);
   return cudaGetLastError();
 }
-
-#define RSGB_POLY_LAUNCHER_NAME(W, M, OP) launch_poly_w##W##_m##M##_op##OP
-#define RSGB_DEFINE_POLY_LAUNCHER(W, M, OP)                                                        \
-  cudaError_t RSGB_POLY_LAUNCHER_NAME(W, M, OP)(const JobParams& p, const LaunchShape& sh,         \
-                                                cudaStream_t st) {                                 \
-    return launch_poly_instance<W, M, OP>(p, sh, st);                                              \
-  }
 
 }  // namespace rsgb

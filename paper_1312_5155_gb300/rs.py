@@ -27,6 +27,13 @@ _lock = threading.Lock()
 _lib = None
 
 VP = ctypes.c_void_p
+RS_OP_ENCODE, RS_OP_DECODE = 0, 1
+
+
+class RsOp(ctypes.Structure):
+    """struct rs_op of include/rs_gb300.h."""
+    _fields_ = [("code", VP), ("op", ctypes.c_int), ("n_erasures", ctypes.c_int),
+                ("erasures", ctypes.c_int * 8), ("blocks", VP * 64), ("block_bytes", ctypes.c_size_t)]
 
 
 class RSError(RuntimeError):
@@ -57,6 +64,13 @@ def lib() -> ctypes.CDLL:
                 "rs_decode": (ctypes.c_int, [VP, ctypes.POINTER(ctypes.c_int), ctypes.c_int,
                                              ctypes.POINTER(VP), ctypes.c_size_t, VP]),
                 "rs_poll_status": (ctypes.c_int, [VP, ctypes.POINTER(ctypes.c_int)]),
+                "rs_batch_create": (ctypes.c_int, [ctypes.c_int, ctypes.POINTER(VP)]),
+                "rs_batch_destroy": (None, [VP]),
+                "rs_batch_set_launch": (ctypes.c_int, [VP, ctypes.c_int, ctypes.c_int, ctypes.c_int]),
+                "rs_batch_set": (ctypes.c_int, [VP, ctypes.POINTER(RsOp), ctypes.c_int, VP]),
+                "rs_batch_launch": (ctypes.c_int, [VP, VP]),
+                "rs_batch_kernel_count": (ctypes.c_int, [VP]),
+                "rs_batch_poll_status": (ctypes.c_int, [VP, ctypes.POINTER(ctypes.c_int)]),
             }
             for name, (res, args) in sig.items():
                 fn = getattr(L, name)
@@ -180,6 +194,104 @@ class Code:
     def close(self):
         if getattr(self, "handle", None):
             rs_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+# ------------------------------------------------------------------ batches
+def rs_batch_create(max_ops: int) -> int:
+    h = VP()
+    _check(lib().rs_batch_create(max_ops, ctypes.byref(h)))
+    return h.value
+
+
+def rs_batch_destroy(handle: int) -> None:
+    lib().rs_batch_destroy(handle)
+
+
+def rs_batch_set_launch(handle: int, consumer_warps: int = 0, depth: int = 0, ctas_per_sm: int = 0) -> None:
+    _check(lib().rs_batch_set_launch(handle, consumer_warps, depth, ctas_per_sm))
+
+
+def make_ops(ops):
+    """ops: iterable of (Code, "encode"|"decode", erasures, blocks, block_bytes)."""
+    ops = list(ops)
+    arr = (RsOp * max(1, len(ops)))()
+    for i, (code, kind, er, blocks, nbytes) in enumerate(ops):
+        o = arr[i]
+        o.code = code.handle
+        o.op = RS_OP_ENCODE if kind == "encode" else RS_OP_DECODE
+        er = list(er or [])
+        if len(er) > 8:
+            raise ValueError("at most 8 erasures")
+        o.n_erasures = len(er)
+        for j, x in enumerate(er):
+            o.erasures[j] = x
+        blocks = list(blocks)
+        if len(blocks) > 64:
+            raise ValueError("at most 64 blocks")
+        for j, b in enumerate(blocks):
+            o.blocks[j] = _ptr(b)
+        o.block_bytes = nbytes
+    return arr, len(ops)
+
+
+def rs_batch_set(handle: int, ops, stream=None) -> None:
+    arr, n = ops if isinstance(ops, tuple) else make_ops(ops)
+    _check(lib().rs_batch_set(handle, arr, n, _stream(stream)))
+
+
+def rs_batch_launch(handle: int, stream=None) -> None:
+    _check(lib().rs_batch_launch(handle, _stream(stream)))
+
+
+def rs_batch_kernel_count(handle: int) -> int:
+    return lib().rs_batch_kernel_count(handle)
+
+
+def rs_batch_poll_status(handle: int) -> int:
+    v = ctypes.c_int(0)
+    rc = lib().rs_batch_poll_status(handle, ctypes.byref(v))
+    if rc not in (0, 5):
+        _check(rc)
+    return v.value
+
+
+class Batch:
+    """Many stripe operations launched together (one persistent kernel per
+    kernel group).  Keeps the Code objects of its ops alive."""
+
+    def __init__(self, max_ops: int):
+        self.max_ops = max_ops
+        self.handle = rs_batch_create(max_ops)
+        self._codes = []
+
+    def set_launch(self, consumer_warps=0, depth=0, ctas_per_sm=0):
+        rs_batch_set_launch(self.handle, consumer_warps, depth, ctas_per_sm)
+
+    def set(self, ops, stream=None):
+        ops = list(ops)
+        self._codes = [o[0] for o in ops]
+        rs_batch_set(self.handle, make_ops(ops), stream)
+
+    def launch(self, stream=None):
+        rs_batch_launch(self.handle, stream)
+
+    @property
+    def kernel_count(self) -> int:
+        return rs_batch_kernel_count(self.handle)
+
+    def poll_status(self) -> int:
+        return rs_batch_poll_status(self.handle)
+
+    def close(self):
+        if getattr(self, "handle", None):
+            rs_batch_destroy(self.handle)
             self.handle = None
 
     def __del__(self):

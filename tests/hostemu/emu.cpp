@@ -10,6 +10,7 @@
 #include <string>
 #include <vector>
 
+#include "codec_matrix.hpp"
 #include "codec_poly.hpp"
 #include "job.hpp"
 #include "plan.hpp"
@@ -109,9 +110,182 @@ int decode_w(const DecodePlan& pl, uint8_t* blocks, size_t B) {
   return -1;
 }
 
+// Packet layout: the thread's W words are word u of the W packets of one
+// super-packet.
+template <int W>
+struct HostPacketTile {
+  const uint8_t* const* in;
+  uint8_t* const* out;
+  size_t sp_off;
+  size_t P;
+  size_t u;
+  void load(int i, uint32_t* x) {
+    for (int c = 0; c < W; ++c) {
+      const uint8_t* p = in[i] + sp_off + (size_t)c * P + 4 * u;
+      x[c] = p[0] | (p[1] << 8) | (p[2] << 16) | ((uint32_t)p[3] << 24);
+    }
+  }
+  void store(int t, const uint32_t* x) {
+    for (int c = 0; c < W; ++c) {
+      uint8_t* p = out[t] + sp_off + (size_t)c * P + 4 * u;
+      for (int q = 0; q < 4; ++q) p[q] = (uint8_t)(x[c] >> (8 * q));
+    }
+  }
+};
+
+template <int W, int M>
+struct HostCols {
+  const std::vector<uint32_t>* P;
+  int k;
+  uint32_t mask(int j, int i, int c) const { return (((*P)[(size_t)i * k + j] >> c) & 1u) ? 0xFFFFFFFFu : 0u; }
+};
+
+// Runs `body(tile)` over every 32-column group of the stripe in the layout.
+template <int W, bool kPacket, class F>
+void for_groups(const std::vector<const uint8_t*>& in, const std::vector<uint8_t*>& out, size_t B, size_t P, F&& body) {
+  if (kPacket) {
+    for (size_t sp = 0; sp < B; sp += (size_t)W * P)
+      for (size_t u = 0; u < P / 4; ++u) {
+        HostPacketTile<W> t{in.data(), out.data(), sp, P, u};
+        body(t);
+      }
+  } else {
+    const size_t segb = segment_bytes(W);
+    for (size_t seg = 0; seg < B; seg += segb)
+      for (int lane = 0; lane < 32; ++lane) {
+        HostTile<W> t{in.data(), out.data(), B, seg, lane};
+        body(t);
+      }
+  }
+}
+
+template <int W, int M, bool kPacket>
+int mat_runtime(int k, const std::vector<uint32_t>& P, bool decode, const DecodePlan* pl, uint8_t* blocks, size_t B,
+                size_t pkt) {
+  std::vector<const uint8_t*> in;
+  std::vector<uint8_t*> out;
+  HostCols<W, M> cols{&P, k};
+  if (!decode) {
+    for (int j = 0; j < k; ++j) in.push_back(blocks + (size_t)j * B);
+    for (int i = 0; i < M; ++i) out.push_back(blocks + (size_t)(k + i) * B);
+    for_groups<W, kPacket>(in, out, B, pkt, [&](auto& t) { MatEncodeRuntime<W, M, !kPacket>::run(k, t, t, cols); });
+  } else {
+    for (int b : pl->in_blocks) in.push_back(blocks + (size_t)b * B);
+    for (int b : pl->out_blocks) out.push_back(blocks + (size_t)b * B);
+    HostCoef<W, M> cf{pl};
+    for_groups<W, kPacket>(in, out, B, pkt, [&](auto& t) {
+      MatDecodeRuntime<W, M, !kPacket>::run(k, pl->read_mask, pl->e, t, t, cols, cf);
+    });
+  }
+  return 0;
+}
+
+template <int W, int K, int M, int KIND>
+int mat_fixed(bool decode, const DecodePlan* pl, uint8_t* blocks, size_t B, size_t pkt) {
+  constexpr bool kPacket = KIND == kKindCauchy;
+  std::vector<const uint8_t*> in;
+  std::vector<uint8_t*> out;
+  if (!decode) {
+    for (int j = 0; j < K; ++j) in.push_back(blocks + (size_t)j * B);
+    for (int i = 0; i < M; ++i) out.push_back(blocks + (size_t)(K + i) * B);
+    for_groups<W, kPacket>(in, out, B, pkt, [&](auto& t) { MatEncodeFixed<W, K, M, KIND, !kPacket>::run(t, t); });
+  } else {
+    for (int b : pl->in_blocks) in.push_back(blocks + (size_t)b * B);
+    for (int b : pl->out_blocks) out.push_back(blocks + (size_t)b * B);
+    HostCoef<W, M> cf{pl};
+    for_groups<W, kPacket>(in, out, B, pkt, [&](auto& t) {
+      MatDecodeFixed<W, K, M, KIND, !kPacket>::run(pl->read_mask, pl->e, t, t, cf);
+    });
+  }
+  return 0;
+}
+
+template <int W, bool kPacket>
+int mat_runtime_m(int k, int m, const std::vector<uint32_t>& P, bool decode, const DecodePlan* pl, uint8_t* blocks,
+                  size_t B, size_t pkt) {
+  switch (m) {
+    case 1: return mat_runtime<W, 1, kPacket>(k, P, decode, pl, blocks, B, pkt);
+    case 2: return mat_runtime<W, 2, kPacket>(k, P, decode, pl, blocks, B, pkt);
+    case 3: return mat_runtime<W, 3, kPacket>(k, P, decode, pl, blocks, B, pkt);
+    case 4: return mat_runtime<W, 4, kPacket>(k, P, decode, pl, blocks, B, pkt);
+    case 5: return mat_runtime<W, 5, kPacket>(k, P, decode, pl, blocks, B, pkt);
+    case 6: return mat_runtime<W, 6, kPacket>(k, P, decode, pl, blocks, B, pkt);
+    case 7: return mat_runtime<W, 7, kPacket>(k, P, decode, pl, blocks, B, pkt);
+    case 8: return mat_runtime<W, 8, kPacket>(k, P, decode, pl, blocks, B, pkt);
+  }
+  return -1;
+}
+
+template <int KIND>
+int mat_fixed_dispatch(int w, int k, int m, bool decode, const DecodePlan* pl, uint8_t* b, size_t B, size_t pkt) {
+  if (w == 8 && k == 6 && m == 3) return mat_fixed<8, 6, 3, KIND>(decode, pl, b, B, pkt);
+  if (w == 8 && k == 10 && m == 4) return mat_fixed<8, 10, 4, KIND>(decode, pl, b, B, pkt);
+  if (w == 8 && k == 12 && m == 4) return mat_fixed<8, 12, 4, KIND>(decode, pl, b, B, pkt);
+  if (w == 8 && k == 20 && m == 4) return mat_fixed<8, 20, 4, KIND>(decode, pl, b, B, pkt);
+  if (w == 16 && k == 12 && m == 4) return mat_fixed<16, 12, 4, KIND>(decode, pl, b, B, pkt);
+  return -2;
+}
+
 }  // namespace
 
 extern "C" {
+
+// Matrix realizations: kind 1 = Vandermonde (symbol layout), 2 = Cauchy
+// (packet layout, packet bytes pkt).  fixed: compile-time P kernels (only
+// for the registered codes), else runtime P.  er/e: decode when e > 0.
+int emu_mat(int w, int k, int m, int kind, int fixed, const int* er, int e, int read_all, uint8_t* blocks, size_t B,
+            size_t pkt) {
+  std::vector<uint32_t> P;
+  if (kind == 1) {
+    if (!vandermonde_parity_matrix(k, m, w, P)) return -3;
+  } else {
+    cauchy_parity_matrix(k, m, w, P);
+  }
+  DecodePlan pl;
+  const bool decode = e > 0;
+  if (decode) {
+    std::string err;
+    if (!make_matrix_decode_plan(k, m, w, P, er, e, read_all != 0, pl, err)) return -1;
+  }
+  const DecodePlan* plp = decode ? &pl : nullptr;
+  if (fixed) return kind == 1 ? mat_fixed_dispatch<1>(w, k, m, decode, plp, blocks, B, pkt)
+                              : mat_fixed_dispatch<2>(w, k, m, decode, plp, blocks, B, pkt);
+  const bool packet = kind == 2;
+  if (w == 8) return packet ? mat_runtime_m<8, true>(k, m, P, decode, plp, blocks, B, pkt)
+                            : mat_runtime_m<8, false>(k, m, P, decode, plp, blocks, B, pkt);
+  return packet ? mat_runtime_m<16, true>(k, m, P, decode, plp, blocks, B, pkt)
+                : mat_runtime_m<16, false>(k, m, P, decode, plp, blocks, B, pkt);
+}
+
+// Host copy of the parity matrix the library builds (for the tests).
+int emu_parity_matrix(int w, int k, int m, int kind, uint32_t* out) {
+  std::vector<uint32_t> P;
+  if (kind == 1) {
+    if (!vandermonde_parity_matrix(k, m, w, P)) return -3;
+  } else {
+    cauchy_parity_matrix(k, m, w, P);
+  }
+  for (size_t i = 0; i < P.size(); ++i) out[i] = P[i];
+  return 0;
+}
+
+// Compile-time parity matrix of a registered code (for the tests).
+int emu_fixed_parity_matrix(int w, int k, int m, int kind, uint32_t* out) {
+  auto copy = [&](const auto& mat, int K, int M) {
+    for (int i = 0; i < M; ++i)
+      for (int j = 0; j < K; ++j) out[i * K + j] = mat.a[i][j];
+    return 0;
+  };
+  if (kind == 1) {
+    if (w == 8 && k == 10 && m == 4) return copy(ParityMatrix<8, 10, 4, 1>::value, 10, 4);
+    if (w == 8 && k == 20 && m == 4) return copy(ParityMatrix<8, 20, 4, 1>::value, 20, 4);
+    if (w == 16 && k == 12 && m == 4) return copy(ParityMatrix<16, 12, 4, 1>::value, 12, 4);
+  } else {
+    if (w == 8 && k == 10 && m == 4) return copy(ParityMatrix<8, 10, 4, 2>::value, 10, 4);
+    if (w == 16 && k == 12 && m == 4) return copy(ParityMatrix<16, 12, 4, 2>::value, 12, 4);
+  }
+  return -2;
+}
 
 int emu_poly_encode(int w, int k, int m, uint8_t* blocks, size_t B) {
   return w == 8 ? encode_w<8>(k, m, blocks, B) : (w == 16 ? encode_w<16>(k, m, blocks, B) : -1);

@@ -1,0 +1,118 @@
+"""CPU checks of the library's matrix-realization codecs (Vandermonde in
+the symbol layout, Cauchy in the packet layout), compile-time and runtime P,
+against the oracle."""
+import ctypes
+import itertools
+
+import numpy as np
+import pytest
+
+from oracle import oracle as O
+from paper_1312_5155_gb300 import inputs
+from tests.hostemu.build import build
+
+U8P = ctypes.POINTER(ctypes.c_uint8)
+KIND = {"vandermonde": 1, "cauchy": 2}
+FIXED = {(8, 6, 3), (8, 10, 4), (8, 12, 4), (8, 20, 4), (16, 12, 4)}
+
+
+@pytest.fixture(scope="module")
+def emu():
+    L = build()
+    L.emu_mat.argtypes = [ctypes.c_int] * 5 + [ctypes.POINTER(ctypes.c_int), ctypes.c_int, ctypes.c_int, U8P,
+                                               ctypes.c_size_t, ctypes.c_size_t]
+    L.emu_parity_matrix.argtypes = [ctypes.c_int] * 4 + [ctypes.POINTER(ctypes.c_uint32)]
+    L.emu_fixed_parity_matrix.argtypes = [ctypes.c_int] * 4 + [ctypes.POINTER(ctypes.c_uint32)]
+    return L
+
+
+def run(L, real, w, k, m, fixed, er, blocks, pkt, read_all=False):
+    arr = (ctypes.c_int * max(1, len(er)))(*er)
+    rc = L.emu_mat(w, k, m, KIND[real], int(fixed), arr, len(er), int(read_all), blocks.ctypes.data_as(U8P),
+                   blocks.shape[1], pkt)
+    assert rc == 0, rc
+
+
+@pytest.mark.parametrize("real", ["vandermonde", "cauchy"])
+@pytest.mark.parametrize("w,k,m", [(8, 10, 4), (8, 6, 3), (16, 12, 4), (8, 5, 7), (8, 20, 4), (16, 3, 2)])
+def test_host_parity_matrix_matches_oracle(emu, real, w, k, m):
+    out = (ctypes.c_uint32 * (k * m))()
+    assert emu.emu_parity_matrix(w, k, m, KIND[real], out) == 0
+    got = np.array(list(out), dtype=np.uint32).reshape(m, k)
+    want = O.vand_matrix(w, k, m)[k:] if real == "vandermonde" else O.cauchy_matrix(w, k, m)
+    assert np.array_equal(got, want)
+
+
+@pytest.mark.parametrize("real", ["vandermonde", "cauchy"])
+@pytest.mark.parametrize("w,k,m", [(8, 10, 4), (16, 12, 4), (8, 20, 4)])
+def test_compile_time_parity_matrix_matches_oracle(emu, real, w, k, m):
+    out = (ctypes.c_uint32 * (k * m))()
+    rc = emu.emu_fixed_parity_matrix(w, k, m, KIND[real], out)
+    if rc == -2:
+        pytest.skip("not exported by the harness")
+    got = np.array(list(out), dtype=np.uint32).reshape(m, k)
+    want = O.vand_matrix(w, k, m)[k:] if real == "vandermonde" else O.cauchy_matrix(w, k, m)
+    assert np.array_equal(got, want)
+
+
+def make_stripe(w, k, m, B, seed=3, stripe=0):
+    blocks = np.zeros((k + m, B), dtype=np.uint8)
+    blocks[:k] = inputs.stripe_blocks(seed, stripe, k, B)
+    return blocks
+
+
+CASES = [("vandermonde", 8, 10, 4, 4096 + 48, 0), ("vandermonde", 8, 6, 3, 3000, 0),
+         ("vandermonde", 16, 12, 4, 8192 + 2, 0), ("vandermonde", 8, 5, 7, 2048, 0),
+         ("vandermonde", 8, 20, 4, 1100, 0),
+         ("cauchy", 8, 10, 4, 8 * 256 * 2, 256), ("cauchy", 8, 6, 3, 8 * 128 * 3, 128),
+         ("cauchy", 16, 12, 4, 16 * 128 * 2, 128), ("cauchy", 8, 5, 7, 8 * 384, 384),
+         ("cauchy", 8, 20, 4, 8 * 128, 128)]
+
+
+@pytest.mark.parametrize("real,w,k,m,B,pkt", CASES)
+def test_encode_matches_oracle(emu, real, w, k, m, B, pkt):
+    base = make_stripe(w, k, m, B)
+    ref = base.copy()
+    O.encode(real, w, k, m, ref, packet_bytes=pkt or 2048)
+    for fixed in (False, True):
+        if fixed and (w, k, m) not in FIXED:
+            continue
+        got = base.copy()
+        got[k:] = 0x44
+        run(emu, real, w, k, m, fixed, [], got, pkt)
+        assert np.array_equal(got, ref), fixed
+
+
+@pytest.mark.parametrize("read_all", [False, True])
+@pytest.mark.parametrize("real,w,k,m,B,pkt", CASES)
+def test_decode_seeded_patterns(emu, real, w, k, m, B, pkt, read_all):
+    base = make_stripe(w, k, m, B)
+    O.encode(real, w, k, m, base, packet_bytes=pkt or 2048)
+    n = k + m
+    for stripe in range(2 * m):
+        e = 1 + stripe % m
+        er = inputs.erasure_pattern(11, stripe, n, e)
+        for fixed in (False, True):
+            if fixed and (w, k, m) not in FIXED:
+                continue
+            got = base.copy()
+            got[er] = 0x99
+            run(emu, real, w, k, m, fixed, er, got, pkt, read_all)
+            assert np.array_equal(got, base), (er, fixed)
+
+
+@pytest.mark.parametrize("real", ["vandermonde", "cauchy"])
+def test_decode_every_pattern_rs_6_3(emu, real):
+    w, k, m = 8, 6, 3
+    pkt = 128
+    B = 8 * pkt
+    base = make_stripe(w, k, m, B)
+    O.encode(real, w, k, m, base, packet_bytes=pkt)
+    n = k + m
+    for e in range(1, m + 1):
+        for er in itertools.combinations(range(n), e):
+            for fixed in (False, True):
+                got = base.copy()
+                got[list(er)] = 0
+                run(emu, real, w, k, m, fixed, list(er), got, pkt, read_all=(e % 2 == 0))
+                assert np.array_equal(got, base), (er, fixed)
