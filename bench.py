@@ -121,15 +121,15 @@ def op_bytes(op: str) -> int:
 class Workload:
     """Device-resident stripes and the batches that encode / decode them."""
 
-    def __init__(self, rank: int, device):
+    def __init__(self, rank: int, device, tune: bool = True):
         import torch
 
-        from paper_1312_5155_gb300 import inputs, rs
+        from paper_1312_5155_gb300 import autotune, inputs, rs
 
         self.S = n_stripes()
         self.n = K + M
         seed = inputs.config_seed(CONFIG)
-        self.bufs, self.batches, self.codes, self.ers = {}, {}, {}, []
+        self.bufs, self.batches, self.codes, self.ers, self.ops, self.shapes = {}, {}, {}, [], {}, {}
         data = torch.empty((self.S, K, BLOCK), dtype=torch.uint8, device=device)
         for s in range(self.S):
             gs = rank * self.S + s
@@ -140,15 +140,30 @@ class Workload:
             buf = torch.empty((self.S, self.n, BLOCK), dtype=torch.uint8, device=device)
             buf[:, :K] = data
             rows = [list(buf[s]) for s in range(self.S)]
+            enc_ops = [(code, "encode", [], rows[s], BLOCK) for s in range(self.S)]
+            dec_ops = [(code, "decode", self.ers[s], rows[s], BLOCK) for s in range(self.S)]
             enc = rs.Batch(self.S)
-            enc.set([(code, "encode", [], rows[s], BLOCK) for s in range(self.S)])
+            enc.set(enc_ops)
             dec = rs.Batch(self.S)
-            dec.set([(code, "decode", self.ers[s], rows[s], BLOCK) for s in range(self.S)])
+            dec.set(dec_ops)
             self.codes[real], self.bufs[real], self.batches[real] = code, buf, (enc, dec)
+            self.ops[real] = (enc_ops, dec_ops)
         del data
         torch.cuda.synchronize()
         for real in REALIZATIONS:  # valid parity before any decode
             self.batches[real][0].launch()
+        torch.cuda.synchronize()
+        # launch shapes chosen by the autotuner (outside any timed region)
+        sms = torch.cuda.get_device_properties(device).multi_processor_count
+        for real in REALIZATIONS:
+            for i, op in enumerate(("encode", "decode")):
+                b = self.batches[real][i]
+                if tune:
+                    key = autotune.make_key(f"batch{self.S}-{op}", real, K, M, W, BLOCK, sms)
+                    shape, _ = autotune.tune_batch(b, self.ops[real][i], key=key)
+                else:
+                    shape = (8, 16, 1)
+                self.shapes[f"{real}_{op}"] = list(shape)
         torch.cuda.synchronize()
 
     def launches(self):
@@ -158,7 +173,7 @@ class Workload:
 def run_ours(args, rank, world, device):
     import torch
 
-    wl = Workload(rank, device)
+    wl = Workload(rank, device, tune=not args.no_tune)
     st = torch.cuda.current_stream()
     names = [(real, op) for real in REALIZATIONS for op in ("encode", "decode")]
 
@@ -229,6 +244,8 @@ def run_ours(args, rank, world, device):
         "ops": ops,
         "roofline": {"bound": "hbm", "kernel": f"{dom[0]}_{dom[1]}", "achieved": dom_gbs, "peak": peak,
                      "peak_kind": kind, "unit": "GB/s", "frac": round(dom_gbs / peak, 4), "traffic": None},
+        "launch_shapes": {k2: {"consumer_warps": v[0], "depth": v[1], "ctas_per_sm": v[2]}
+                          for k2, v in wl.shapes.items()},
         "gpu_launches": args.steps * wl.launches(),
         "device_status": status,
         "clocks": clocks,
@@ -360,6 +377,37 @@ def run_reference(args, rank, world):
     }
 
 
+def profile_case(name: str, stripes: int = 16, launches: int = 3):
+    """Small case of one bench kernel for ncu: `stripes` stripes of the bench
+    geometry (RS(10,4), 1 MiB blocks; 16 stripes = 224 MiB, larger than L2),
+    one realization, `launches` batched launches of one op (after one
+    encode that makes the parity valid)."""
+    import torch
+
+    from paper_1312_5155_gb300 import inputs, rs
+
+    real, op = name.rsplit("_", 1)
+    seed = inputs.config_seed(CONFIG)
+    n = K + M
+    code = rs.Code(K, M, W, real, packet_bytes=PACKET if real == "cauchy" else None)
+    buf = torch.empty((stripes, n, BLOCK), dtype=torch.uint8, device="cuda")
+    buf[:, :K] = inputs.random_bytes_torch(seed, 0, stripes * K * BLOCK, "cuda").view(stripes, K, BLOCK)
+    rows = [list(buf[s]) for s in range(stripes)]
+    enc = rs.Batch(stripes)
+    enc.set([(code, "encode", [], rows[s], BLOCK) for s in range(stripes)])
+    enc.launch()
+    b = enc
+    if op == "decode":
+        b = rs.Batch(stripes)
+        b.set([(code, "decode", inputs.erasure_pattern(seed, s, n, M), rows[s], BLOCK) for s in range(stripes)])
+    for _ in range(launches):
+        b.launch()
+    torch.cuda.synchronize()
+    if b.poll_status() != 0:
+        raise SystemExit("device status word set")
+    print(f"profile case {name}: {launches} launches of {stripes} stripes done")
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -368,7 +416,13 @@ def main():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-tune", action="store_true", help="skip the launch-shape autotuner")
+    ap.add_argument("--profile-case", default=None,
+                    help="run one small kernel case for ncu, e.g. poly_encode, cauchy_decode")
     args = ap.parse_args()
+    if args.profile_case:
+        profile_case(args.profile_case)
+        return
 
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))

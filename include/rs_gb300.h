@@ -12,8 +12,9 @@
  *     forms one column (one codeword); w = 8 symbols are bytes, w = 16
  *     symbols are little-endian 16-bit words.
  *   - Pointers: every block pointer is a DEVICE pointer, 16-byte aligned,
- *     owned by the caller.  Pointer arrays are HOST arrays, read during the
- *     call only.  Input and output blocks must not overlap.
+ *     owned by the caller (with block_bytes = 0 nothing is accessed and any
+ *     pointer, NULL included, is accepted).  Pointer arrays are HOST arrays,
+ *     read during the call only.  Input and output blocks must not overlap.
  *   - Streams: `stream` is a cudaStream_t (NULL = legacy default stream).
  *     Work is enqueued asynchronously; the call returns once it is enqueued.
  *   - Errors: argument errors are detected on the host, return before any

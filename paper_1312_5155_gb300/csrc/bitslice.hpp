@@ -23,6 +23,22 @@
 
 namespace rsgb {
 
+// Shifts by a constant, written as multiplies so that on the GPU they run
+// on the FMA pipe (IMAD / IMAD.HI) and leave the integer-logic pipe, which
+// bounds these kernels, to the XORs.
+template <int S>
+RS_HD uint32_t shl_fma(uint32_t x) {
+  return x * (1u << S);
+}
+template <int S>
+RS_HD uint32_t shr_fma(uint32_t x) {
+#if defined(__CUDA_ARCH__)
+  return __umulhi(x, 1u << (32 - S));
+#else
+  return x >> S;
+#endif
+}
+
 // x[i], x[i+D] for all i with bit D clear: exchange the bits of x[i] above
 // the mask with the bits of x[i+D] below it.
 template <int N, int D, int S, uint32_t MASK>
@@ -39,8 +55,8 @@ RS_HD void swap_round(uint32_t* x) {
         continue;
       }
 #endif
-      x[i] = (lo & MASK) | ((hi << S) & ~MASK);
-      x[i + D] = ((lo >> S) & MASK) | (hi & ~MASK);
+      x[i] = (lo & MASK) | (shl_fma<S>(hi) & ~MASK);
+      x[i + D] = (shr_fma<S>(lo) & MASK) | (hi & ~MASK);
     }
   }
 }
@@ -97,25 +113,6 @@ RS_HD void mul_alpha(uint32_t* x) {
   for (int r = 1; r < W; ++r) {
     if ((low >> r) & 1u) x[r] ^= top;
   }
-}
-
-// Runtime constant e given as W masks: mask[c] = ~0 if bit c of e is set.
-// acc ^= e * in, computed as sum_c bit_c(e) * (alpha^c * in).  `chain` is
-// clobbered (it walks in, alpha*in, alpha^2*in, ...).
-template <int W>
-RS_HD void mul_acc_masked(uint32_t* acc, uint32_t* chain, const uint32_t* mask) {
-#pragma unroll
-  for (int c = 0; c < W; ++c) {
-    const uint32_t mk = mask[c];
-#pragma unroll
-    for (int r = 0; r < W; ++r) acc[r] ^= chain[r] & mk;
-    if (c + 1 < W) mul_alpha<W>(chain);
-  }
-}
-
-// Masks of a runtime constant e (host side): mask[c] = -(bit c of e).
-RS_HD void expand_masks(uint32_t e, int w, uint32_t* mask) {
-  for (int c = 0; c < w; ++c) mask[c] = ((e >> c) & 1u) ? 0xFFFFFFFFu : 0u;
 }
 
 }  // namespace rsgb

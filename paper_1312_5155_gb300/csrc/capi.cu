@@ -96,6 +96,7 @@ bool disjoint(const std::vector<const void*>& ptrs, size_t bytes) {
 }
 
 rs_status check_blocks(const rs_code* c, const std::vector<const void*>& ptrs, size_t bytes) {
+  if (bytes == 0) return RS_OK;  // nothing is read or written: any pointers do
   for (size_t i = 0; i < ptrs.size(); ++i) {
     if (!ptrs[i]) return fail(RS_EINVAL, "null block pointer");
     if (!aligned16(ptrs[i])) return fail(RS_EINVAL, "block pointers must be 16-byte aligned");
@@ -232,7 +233,7 @@ rs_status prepare_decode(rs_code* c, const int* er, int e, void* const* blocks, 
   for (int t = 0; t < pl.e; ++t)
     for (int j = 0; j < M; ++j)
       for (int b = 0; b < c->w; ++b)
-        po.coef[(size_t)(t * M + j) * c->w + b] = ((pl.W[t][j] >> b) & 1u) ? 0xFFFFFFFFu : 0u;
+        po.coef[(size_t)(t * M + j) * c->w + b] = (pl.W[t][j] >> b) & 1u;
   return RS_OK;
 }
 
@@ -388,12 +389,11 @@ rs_status rs_init(int k, int m, int w, int realization, rs_code** out) {
   if (e == cudaSuccess) e = cudaMalloc(&c->d_status, sizeof(int));
   if (e == cudaSuccess) e = cudaMemset(c->d_status, 0, sizeof(int));
   if (e == cudaSuccess && c->real != Realization::Poly) {
-    // column masks [j][i][b] of P for the runtime-P kernels
+    // column bit words [j][i][b] of P for the runtime-P kernels
     std::vector<uint32_t> masks((size_t)k * m * w);
     for (int j = 0; j < k; ++j)
       for (int i = 0; i < m; ++i)
-        for (int b = 0; b < w; ++b)
-          masks[((size_t)j * m + i) * w + b] = ((c->P[(size_t)i * k + j] >> b) & 1u) ? 0xFFFFFFFFu : 0u;
+        for (int b = 0; b < w; ++b) masks[((size_t)j * m + i) * w + b] = (c->P[(size_t)i * k + j] >> b) & 1u;
     e = cudaMalloc(&c->d_pmask, masks.size() * sizeof(uint32_t));
     if (e == cudaSuccess)
       e = cudaMemcpy(c->d_pmask, masks.data(), masks.size() * sizeof(uint32_t), cudaMemcpyHostToDevice);

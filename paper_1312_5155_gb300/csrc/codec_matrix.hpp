@@ -195,18 +195,27 @@ struct MatDecodeFixed {
 };
 
 // ------------------------------------------------ runtime P (any code)
-// cols.mask(b, i, c): W masks of P[i][b] (data block b, parity row i).
+// cols.bit(b, i, c): bit c (0 or 1) of P[i][b] (data block b, parity row i).
+// x is clobbered (it walks x, alpha x, alpha^2 x, ...).
 template <int W, int M, class Cols>
 RS_HD void accumulate_column(uint32_t (*acc)[W], uint32_t* x, int b, const Cols& cols) {
 #pragma unroll
-  for (int c = 0; c < W; ++c) {
+  for (int c = 0; c < W; c += 2) {
+    uint32_t nx[W];
+#pragma unroll
+    for (int r = 0; r < W; ++r) nx[r] = x[r];
+    mul_alpha<W>(nx);
 #pragma unroll
     for (int i = 0; i < M; ++i) {
-      const uint32_t mk = cols.mask(b, i, c);
+      const uint32_t b0 = cols.bit(b, i, c), b1 = cols.bit(b, i, c + 1);
 #pragma unroll
-      for (int r = 0; r < W; ++r) acc[i][r] ^= x[r] & mk;
+      for (int r = 0; r < W; ++r) acc[i][r] ^= (x[r] * b0) ^ (nx[r] * b1);
     }
-    if (c + 1 < W) mul_alpha<W>(x);
+    if (c + 2 < W) {
+#pragma unroll
+      for (int r = 0; r < W; ++r) x[r] = nx[r];
+      mul_alpha<W>(x);
+    }
   }
 }
 

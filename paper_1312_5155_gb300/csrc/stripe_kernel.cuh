@@ -209,18 +209,18 @@ struct PacketTile {
   }
 };
 
-// Runtime matrix W[t][j] as masks, layout [t][j][c] with dims M x M x W.
+// Runtime matrix W[t][j] as bit words (0/1), layout [t][j][c], M x M x W.
 template <int W, int M>
 struct CoefMasks {
   const uint32_t* base;
-  __device__ __forceinline__ uint32_t mask(int t, int j, int c) const { return base[(t * M + j) * W + c]; }
+  __device__ __forceinline__ uint32_t bit(int t, int j, int c) const { return base[(t * M + j) * W + c]; }
 };
 
-// Runtime parity matrix P as masks, layout [j][i][c] with dims k x m x W.
+// Runtime parity matrix P as bit words (0/1), layout [j][i][c], k x m x W.
 template <int W, int M>
 struct ColumnMasks {
   const uint32_t* base;
-  __device__ __forceinline__ uint32_t mask(int j, int i, int c) const { return base[(j * M + i) * W + c]; }
+  __device__ __forceinline__ uint32_t bit(int j, int i, int c) const { return base[(j * M + i) * W + c]; }
 };
 
 // ------------------------------------------------------------------ bodies

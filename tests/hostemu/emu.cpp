@@ -48,7 +48,7 @@ struct HostTile {
 template <int W, int M>
 struct HostCoef {
   const DecodePlan* pl;
-  uint32_t mask(int t, int j, int c) const { return ((pl->W[t][j] >> c) & 1u) ? 0xFFFFFFFFu : 0u; }
+  uint32_t bit(int t, int j, int c) const { return (pl->W[t][j] >> c) & 1u; }
 };
 
 template <int W, int M>
@@ -137,7 +137,7 @@ template <int W, int M>
 struct HostCols {
   const std::vector<uint32_t>* P;
   int k;
-  uint32_t mask(int j, int i, int c) const { return (((*P)[(size_t)i * k + j] >> c) & 1u) ? 0xFFFFFFFFu : 0u; }
+  uint32_t bit(int j, int i, int c) const { return ((*P)[(size_t)i * k + j] >> c) & 1u; }
 };
 
 // Runs `body(tile)` over every 32-column group of the stripe in the layout.
