@@ -115,6 +115,19 @@ rs_status rs_encode(rs_code *code, const void *const *data_ptrs, void *const *pa
 rs_status rs_decode(rs_code *code, const int *erasures, int n_erasures, void *const *block_ptrs,
                     size_t block_bytes, void *stream);
 
+/* Bound of every device-side pipeline wait of this code's kernels, in
+ * nanoseconds (0 = default, 2 s; at most 60 s).  A wait that runs out sets
+ * the status word (see rs_poll_status) and the kernel returns early. */
+rs_status rs_set_wait_limit(rs_code *code, unsigned long long nanoseconds);
+
+/* Test hook for failure detection.  fault = 1: in the next launch of this
+ * code, CTA 0's producer issues no copies, so that CTA's consumers run into
+ * their bounded wait, record the timeout in the status word and return (no
+ * copy is ever in flight for that CTA; other CTAs complete normally; the
+ * affected tile's output is not written).  fault = 0 clears it.  Nothing
+ * faults, traps or hangs: the context stays usable. */
+rs_status rs_inject_fault(rs_code *code, int fault);
+
 /* Read and clear the code's device status word (synchronises the device).
  * *device_status receives 0 or the kernel's error code; the return value is
  * RS_ETIMEOUT when the word was set, RS_OK otherwise. */

@@ -115,4 +115,39 @@ RS_HD void mul_alpha(uint32_t* x) {
   }
 }
 
+// A runtime matrix of field elements held as packed bits in registers.
+// Entry (r, q) of an R x Q matrix is bits [(q*R + r)*W, +W) of the bit
+// string; mask(r, q, c) expands bit c of that entry to 0 / ~0 with two
+// shifts, so the entries cost kWords registers instead of R*Q*W.
+template <int W, int R, int Q>
+struct PackedBits {
+  static constexpr int kWords = (R * Q * W + 31) / 32;
+  uint32_t w[kWords];
+  RS_HD uint32_t mask(int r, int q, int c) const {
+    const int p = (q * R + r) * W + c;
+    return (uint32_t)((int32_t)(w[p >> 5] << (31 - (p & 31))) >> 31);
+  }
+  template <class Src>
+  RS_HD void load(const Src& src) {
+#pragma unroll
+    for (int i = 0; i < kWords; ++i) w[i] = src.word(i);
+  }
+};
+
+// acc[r] ^= sum_q M[r][q] * in_q ... for one input q: acc[r] ^= M[r][q] * x,
+// as sum over c of mask(r, q, c) & (alpha^c x).  x is clobbered.
+template <int W, int R, int Q>
+RS_HD void mul_acc_packed_column(uint32_t (*acc)[W], uint32_t* x, const PackedBits<W, R, Q>& m, int q) {
+#pragma unroll
+  for (int c = 0; c < W; ++c) {
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+      const uint32_t mk = m.mask(r, q, c);
+#pragma unroll
+      for (int b = 0; b < W; ++b) acc[r][b] ^= x[b] & mk;
+    }
+    if (c + 1 < W) mul_alpha<W>(x);
+  }
+}
+
 }  // namespace rsgb

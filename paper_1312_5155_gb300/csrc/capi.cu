@@ -66,6 +66,8 @@ struct rs_code {
   int device = 0;
   int num_sms = 0;
   int* d_status = nullptr;
+  unsigned long long wait_limit_ns = 0;  // 0: kernel default
+  uint32_t inject_next = 0;              // test hook for the next launch
   std::mutex mu;
   std::map<std::vector<int>, DecodePlan> plans;  // key: read mode, erasure list
 };
@@ -228,12 +230,8 @@ rs_status prepare_decode(rs_code* c, const int* er, int e, void* const* blocks, 
   po.ptrs.clear();
   for (int b : pl.in_blocks) po.ptrs.push_back((uint64_t)(uintptr_t)blocks[b]);
   for (int b : pl.out_blocks) po.ptrs.push_back((uint64_t)(uintptr_t)blocks[b]);
-  const int M = pl.M;
-  po.coef.assign((size_t)M * M * c->w, 0u);
-  for (int t = 0; t < pl.e; ++t)
-    for (int j = 0; j < M; ++j)
-      for (int b = 0; b < c->w; ++b)
-        po.coef[(size_t)(t * M + j) * c->w + b] = (pl.W[t][j] >> b) & 1u;
+  po.coef = pack_decode_matrix(pl, c->w);
+  while (po.coef.size() % 4) po.coef.push_back(0u);  // keep every op's words 16-byte aligned
   return RS_OK;
 }
 
@@ -276,6 +274,9 @@ rs_status launch_single(rs_code* c, PreparedOp& po, void* stream) {
   p->n_stripes = 1;
   p->slice_bytes = slice;
   p->depth = depth;
+  p->wait_limit_ns = c->wait_limit_ns;
+  p->inject = c->inject_next;
+  c->inject_next = 0;
   p->inl_stripe = po.d;
   p->inl_stripe.tile_begin = 0;
   p->inl_stripe.ptr_off = 0;
@@ -389,11 +390,8 @@ rs_status rs_init(int k, int m, int w, int realization, rs_code** out) {
   if (e == cudaSuccess) e = cudaMalloc(&c->d_status, sizeof(int));
   if (e == cudaSuccess) e = cudaMemset(c->d_status, 0, sizeof(int));
   if (e == cudaSuccess && c->real != Realization::Poly) {
-    // column bit words [j][i][b] of P for the runtime-P kernels
-    std::vector<uint32_t> masks((size_t)k * m * w);
-    for (int j = 0; j < k; ++j)
-      for (int i = 0; i < m; ++i)
-        for (int b = 0; b < w; ++b) masks[((size_t)j * m + i) * w + b] = (c->P[(size_t)i * k + j] >> b) & 1u;
+    // P's columns as packed bits for the runtime-P kernels
+    const std::vector<uint32_t> masks = pack_columns(c->P, k, m, w);
     e = cudaMalloc(&c->d_pmask, masks.size() * sizeof(uint32_t));
     if (e == cudaSuccess)
       e = cudaMemcpy(c->d_pmask, masks.data(), masks.size() * sizeof(uint32_t), cudaMemcpyHostToDevice);
@@ -462,6 +460,20 @@ rs_status rs_decode(rs_code* c, const int* erasures, int n_erasures, void* const
   rs_status s = prepare_decode(c, erasures, n_erasures, block_ptrs, block_bytes, po);
   if (s != RS_OK) return s;
   return launch_single(c, po, stream);
+}
+
+rs_status rs_set_wait_limit(rs_code* c, unsigned long long nanoseconds) {
+  if (!c) return fail(RS_EINVAL, "code is null");
+  if (nanoseconds > 60ull * 1000000000ull) return fail(RS_EINVAL, "wait limit above 60 s");
+  c->wait_limit_ns = nanoseconds;
+  return ok();
+}
+
+rs_status rs_inject_fault(rs_code* c, int fault) {
+  if (!c) return fail(RS_EINVAL, "code is null");
+  if (fault != 0 && fault != (int)kInjectProducerStall) return fail(RS_EINVAL, "unknown fault");
+  c->inject_next = (uint32_t)fault;
+  return ok();
 }
 
 rs_status rs_poll_status(rs_code* c, int* device_status) {

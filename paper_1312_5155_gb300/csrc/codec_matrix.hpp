@@ -155,6 +155,8 @@ template <int W, int K, int M, int KIND, bool kTranspose>
 struct MatDecodeFixed {
   template <class Src, class Dst, class Coef>
   static RS_HD void run(uint64_t read_mask, int e, Src& src, Dst& dst, Coef& coef) {
+    PackedBits<W, M, M> wm;
+    wm.load(coef);
     uint32_t S[M][W];
 #pragma unroll
     for (int i = 0; i < M; ++i)
@@ -183,7 +185,7 @@ struct MatDecodeFixed {
       }
     }
     uint32_t out[M][W];
-    apply_runtime_matrix<W, M>(out, S, e, coef);
+    apply_runtime_matrix<W, M>(out, S, e, wm);
 #pragma unroll
     for (int t = 0; t < M; ++t) {
       if (t < e) {
@@ -195,30 +197,9 @@ struct MatDecodeFixed {
 };
 
 // ------------------------------------------------ runtime P (any code)
-// cols.bit(b, i, c): bit c (0 or 1) of P[i][b] (data block b, parity row i).
-// x is clobbered (it walks x, alpha x, alpha^2 x, ...).
-template <int W, int M, class Cols>
-RS_HD void accumulate_column(uint32_t (*acc)[W], uint32_t* x, int b, const Cols& cols) {
-#pragma unroll
-  for (int c = 0; c < W; c += 2) {
-    uint32_t nx[W];
-#pragma unroll
-    for (int r = 0; r < W; ++r) nx[r] = x[r];
-    mul_alpha<W>(nx);
-#pragma unroll
-    for (int i = 0; i < M; ++i) {
-      const uint32_t b0 = cols.bit(b, i, c), b1 = cols.bit(b, i, c + 1);
-#pragma unroll
-      for (int r = 0; r < W; ++r) acc[i][r] ^= (x[r] * b0) ^ (nx[r] * b1);
-    }
-    if (c + 2 < W) {
-#pragma unroll
-      for (int r = 0; r < W; ++r) x[r] = nx[r];
-      mul_alpha<W>(x);
-    }
-  }
-}
-
+// cols.column(j) returns a PackedBits<W, M, 1> source for data column j of P
+// (entry (i, 0) = P[i][j]); the column's words are loaded before the input's
+// transpose so their latency overlaps it.
 template <int W, int M, bool kTranspose>
 struct MatEncodeRuntime {
   template <class Src, class Dst, class Cols>
@@ -229,10 +210,12 @@ struct MatEncodeRuntime {
 #pragma unroll
       for (int b = 0; b < W; ++b) acc[i][b] = 0;
     for (int j = 0; j < k; ++j) {
+      PackedBits<W, M, 1> col;
+      col.load(cols.column(j));
       uint32_t x[W];
       src.load(j, x);
       if (kTranspose) transpose<W>(x);
-      accumulate_column<W, M>(acc, x, j, cols);
+      mul_acc_packed_column<W, M, 1>(acc, x, col, 0);
     }
 #pragma unroll
     for (int i = 0; i < M; ++i) {
@@ -252,12 +235,16 @@ struct MatDecodeRuntime {
 #pragma unroll
       for (int b = 0; b < W; ++b) S[i][b] = 0;
     int in = 0;
+    PackedBits<W, M, M> wm;
+    wm.load(coef);
     for (int j = 0; j < k; ++j) {
       if (!((read_mask >> j) & 1ull)) continue;
+      PackedBits<W, M, 1> col;
+      col.load(cols.column(j));
       uint32_t x[W];
       src.load(in++, x);
       if (kTranspose) transpose<W>(x);
-      accumulate_column<W, M>(S, x, j, cols);
+      mul_acc_packed_column<W, M, 1>(S, x, col, 0);
     }
 #pragma unroll
     for (int j = 0; j < M; ++j) {
@@ -270,7 +257,7 @@ struct MatDecodeRuntime {
       }
     }
     uint32_t out[M][W];
-    apply_runtime_matrix<W, M>(out, S, e, coef);
+    apply_runtime_matrix<W, M>(out, S, e, wm);
 #pragma unroll
     for (int t = 0; t < M; ++t) {
       if (t < e) {

@@ -2,7 +2,8 @@
 // bit-planes by one thread.  Host/device code; the caller supplies
 //   src.load(i, x)   : W words of input i (consumption order), as stored
 //   dst.store(t, x)  : W words of output t, as stored
-//   coef.bit(t, j, c) : bit c (0 or 1) of the runtime constant W[t][j]
+//   coef.word(i)     : word i of the runtime matrix W as packed bits
+//                      (PackedBits<W, M, M> layout, entry (t, j))
 #pragma once
 #include "bitslice.hpp"
 
@@ -83,13 +84,12 @@ struct HornerMul<W, M, 0> {
   static RS_HD void run(uint32_t (*)[W]) {}  // alpha^0 = 1
 };
 
-// out[t] = sum_j W[t][j] S_j for t < e.  coef.bit(t, j, c) is bit c of the
-// runtime constant W[t][j] (0 or 1).  For every syndrome j the chain
-// alpha^c S_j (c = 0..W-1) is walked once and shared by all outputs; each
-// pair of chain terms costs two integer multiplies by 0/1 (FMA pipe) and one
-// 3-input XOR (logic pipe) per plane.  S is clobbered.
-template <int W, int M, class Coef>
-RS_HD void apply_runtime_matrix(uint32_t (*out)[W], uint32_t (*S)[W], int e, Coef& coef) {
+// out[t] = sum_j W[t][j] S_j for t < e, with W as packed bits (entry (t, j)).
+// For every syndrome j the chain alpha^c S_j (c = 0..W-1) is walked once and
+// shared by all outputs; each chain term costs one AND-XOR per plane.  S is
+// clobbered.
+template <int W, int M>
+RS_HD void apply_runtime_matrix(uint32_t (*out)[W], uint32_t (*S)[W], int e, const PackedBits<W, M, M>& wm) {
 #pragma unroll
   for (int t = 0; t < M; ++t)
 #pragma unroll
@@ -97,24 +97,16 @@ RS_HD void apply_runtime_matrix(uint32_t (*out)[W], uint32_t (*S)[W], int e, Coe
 #pragma unroll
   for (int j = 0; j < M; ++j) {
 #pragma unroll
-    for (int c = 0; c < W; c += 2) {
-      uint32_t nx[W];
-#pragma unroll
-      for (int b = 0; b < W; ++b) nx[b] = S[j][b];
-      mul_alpha<W>(nx);
+    for (int c = 0; c < W; ++c) {
 #pragma unroll
       for (int t = 0; t < M; ++t) {
         if (t < e) {
-          const uint32_t b0 = coef.bit(t, j, c), b1 = coef.bit(t, j, c + 1);
+          const uint32_t mk = wm.mask(t, j, c);
 #pragma unroll
-          for (int b = 0; b < W; ++b) out[t][b] ^= (S[j][b] * b0) ^ (nx[b] * b1);
+          for (int b = 0; b < W; ++b) out[t][b] ^= S[j][b] & mk;
         }
       }
-      if (c + 2 < W) {
-#pragma unroll
-        for (int b = 0; b < W; ++b) S[j][b] = nx[b];
-        mul_alpha<W>(S[j]);
-      }
+      if (c + 1 < W) mul_alpha<W>(S[j]);
     }
   }
 }
@@ -125,6 +117,8 @@ struct PolyDecode {
   // case the next input (inputs ordered by descending position) holds it.
   template <class Src, class Dst, class Coef>
   static RS_HD void run(int n_pos, uint64_t read_mask, int e, Src& src, Dst& dst, Coef& coef) {
+    PackedBits<W, M, M> wm;  // loaded first: its latency hides behind Step 1
+    wm.load(coef);
     uint32_t S[M][W];
 #pragma unroll
     for (int j = 0; j < M; ++j)
@@ -144,7 +138,7 @@ struct PolyDecode {
       }
     }
     uint32_t out[M][W];
-    apply_runtime_matrix<W, M>(out, S, e, coef);
+    apply_runtime_matrix<W, M>(out, S, e, wm);
 #pragma unroll
     for (int t = 0; t < M; ++t) {
       if (t < e) {

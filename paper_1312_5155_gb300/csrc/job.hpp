@@ -46,6 +46,11 @@ struct StripeDesc {
                         // column masks [j][i][c] (k x m x W words)
 };
 
+// Test hook: CTA 0's producer issues nothing, so that CTA's consumers run
+// into the bounded wait, record the timeout and return (no copy is ever in
+// flight for that CTA, so nothing is left writing its shared memory).
+constexpr uint32_t kInjectProducerStall = 1;
+
 constexpr int kMaxPtrs = kMaxBlocks + kMaxM;
 constexpr int kMaxCoefWords = kMaxM * kMaxM * 16;
 
@@ -59,6 +64,9 @@ struct JobParams {
   uint32_t total_tiles;
   uint32_t slice_bytes;       // bytes of one block per tile
   uint32_t depth;             // ring slots
+  unsigned long long wait_limit_ns;  // bound of every pipeline wait (0 = default 2 s)
+  uint32_t inject;            // test hook: kInjectProducerStall
+  uint32_t pad_inject;
   // one stripe passed by value (single-stripe calls need no device tables)
   StripeDesc inl_stripe;
   uint64_t inl_ptrs[kMaxPtrs];

@@ -59,13 +59,15 @@ __device__ __forceinline__ unsigned long long global_ns() {
   return t;
 }
 
-// Wait for the phase with the given parity to complete; false on timeout.
-__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
+// Wait for the phase with the given parity to complete; false once
+// limit_ns of global time (0 = kWaitLimitNs) or the iteration cap is spent.
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, unsigned long long limit_ns = 0) {
   if (mbar_try_wait(bar, parity)) return true;
+  const unsigned long long limit = limit_ns ? limit_ns : kWaitLimitNs;
   const unsigned long long t0 = global_ns();
   for (uint32_t it = 0; it < kWaitIterCap; ++it) {
     if (mbar_try_wait(bar, parity)) return true;
-    if ((it & 255u) == 255u && global_ns() - t0 > kWaitLimitNs) return false;
+    if ((it & 63u) == 63u && global_ns() - t0 > limit) return false;
   }
   return false;
 }

@@ -159,6 +159,38 @@ bool make_matrix_decode_plan(int k, int m, int w, const std::vector<uint32_t>& P
   return true;
 }
 
+std::vector<uint32_t> pack_bits(const uint32_t* a, int R, int Q, int w) {
+  std::vector<uint32_t> out(((size_t)R * Q * w + 31) / 32, 0u);
+  for (int r = 0; r < R; ++r)
+    for (int q = 0; q < Q; ++q)
+      for (int c = 0; c < w; ++c)
+        if ((a[(size_t)r * Q + q] >> c) & 1u) {
+          const size_t pbit = ((size_t)q * R + r) * w + c;
+          out[pbit >> 5] |= 1u << (pbit & 31);
+        }
+  return out;
+}
+
+std::vector<uint32_t> pack_decode_matrix(const DecodePlan& pl, int w) {
+  const int M = pl.M;
+  std::vector<uint32_t> a((size_t)M * M, 0u);
+  for (int t = 0; t < pl.e; ++t)
+    for (int j = 0; j < M; ++j) a[(size_t)t * M + j] = pl.W[t][j];
+  return pack_bits(a.data(), M, M, w);
+}
+
+std::vector<uint32_t> pack_columns(const std::vector<uint32_t>& P, int k, int m, int w) {
+  const int cw = column_words(m, w);
+  std::vector<uint32_t> out((size_t)k * cw, 0u);
+  std::vector<uint32_t> col(m);
+  for (int j = 0; j < k; ++j) {
+    for (int i = 0; i < m; ++i) col[i] = P[(size_t)i * k + j];
+    const std::vector<uint32_t> words = pack_bits(col.data(), m, 1, w);
+    for (int x = 0; x < cw; ++x) out[(size_t)j * cw + x] = words[x];
+  }
+  return out;
+}
+
 bool vandermonde_parity_matrix(int k, int m, int w, std::vector<uint32_t>& P) {
   // G = V_full * V_top^-1 with V_full[r][c] = r^c (0^0 = 1), §2.2.
   const int n = k + m;

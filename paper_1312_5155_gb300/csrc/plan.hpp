@@ -46,6 +46,18 @@ bool make_matrix_decode_plan(int k, int m, int w, const std::vector<uint32_t>& P
                              const int* erasures, int e, bool read_all, DecodePlan& plan,
                              std::string& err);
 
+// Pack an R x Q matrix of w-bit field elements (row-major in `a`) into the
+// bit layout of PackedBits<W, R, Q>: entry (r, q) at bits [(q*R + r)*w, +w).
+std::vector<uint32_t> pack_bits(const uint32_t* a, int R, int Q, int w);
+
+// Words of the runtime decode matrix W (e used rows of the M x M slot).
+std::vector<uint32_t> pack_decode_matrix(const DecodePlan& pl, int w);
+
+// Words of P's columns for the runtime-P kernels: column j (entries
+// P[0..m-1][j]) occupies column_words(m, w) consecutive words.
+inline int column_words(int m, int w) { return (m * w + 31) / 32; }
+std::vector<uint32_t> pack_columns(const std::vector<uint32_t>& P, int k, int m, int w);
+
 // Parity rows (m x k, row-major) of the systematic generators (§2.2, §2.3).
 bool vandermonde_parity_matrix(int k, int m, int w, std::vector<uint32_t>& P);
 void cauchy_parity_matrix(int k, int m, int w, std::vector<uint32_t>& P);

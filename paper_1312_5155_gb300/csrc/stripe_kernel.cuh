@@ -90,8 +90,9 @@ __device__ __forceinline__ TileGeom tile_geom(const StripeDesc& d, uint32_t lt, 
   return g;
 }
 
-__device__ __forceinline__ void wait_or_fail(uint64_t* bar, uint32_t par, bool& failed, int* status, int code) {
-  if (!failed && !mbar_wait(bar, par)) {
+__device__ __forceinline__ void wait_or_fail(uint64_t* bar, uint32_t par, bool& failed, int* status, int code,
+                                             unsigned long long limit) {
+  if (!failed && !mbar_wait(bar, par, limit)) {
     failed = true;
     record_status(status, code);
   }
@@ -108,6 +109,7 @@ struct SymTile {
   uint32_t seg;    // this warp's segment offset
   uint32_t lane;
   int* status;
+  unsigned long long limit;
   bool failed;
 
   __device__ __forceinline__ void begin(const StripeDesc& d, const TileGeom& g, const uint64_t* p) {
@@ -121,7 +123,7 @@ struct SymTile {
     Ring& r = *ring;
     const uint32_t s = r.s, par = r.par;
     r.advance();
-    wait_or_fail(&r.full[s], par, failed, status, kDevErrTimeoutFull);
+    wait_or_fail(&r.full[s], par, failed, status, kDevErrTimeoutFull, limit);
     const uint8_t* slot = r.slots + (size_t)s * r.slice;
     const uint32_t len16 = len & ~15u;
 #pragma unroll
@@ -179,6 +181,7 @@ struct PacketTile {
   uint32_t P;         // packet bytes
   uint32_t word;      // this thread's 32-bit word inside the span
   int* status;
+  unsigned long long limit;
   bool failed;
 
   __device__ __forceinline__ void begin(const StripeDesc& d, const TileGeom& g, const uint64_t* p) {
@@ -193,7 +196,7 @@ struct PacketTile {
     Ring& r = *ring;
     const uint32_t s = r.s, par = r.par;
     r.advance();
-    wait_or_fail(&r.full[s], par, failed, status, kDevErrTimeoutFull);
+    wait_or_fail(&r.full[s], par, failed, status, kDevErrTimeoutFull, limit);
     const uint8_t* slot = r.slots + (size_t)s * r.slice;
 #pragma unroll
     for (int c = 0; c < W; ++c)
@@ -209,35 +212,47 @@ struct PacketTile {
   }
 };
 
-// Runtime matrix W[t][j] as bit words (0/1), layout [t][j][c], M x M x W.
-template <int W, int M>
-struct CoefMasks {
+// Runtime decode matrix W as packed bits (PackedBits<W, M, M> layout).
+struct CoefWords {
   const uint32_t* base;
-  __device__ __forceinline__ uint32_t bit(int t, int j, int c) const { return base[(t * M + j) * W + c]; }
+  __device__ __forceinline__ uint32_t word(int i) const { return base[i]; }
 };
 
-// Runtime parity matrix P as bit words (0/1), layout [j][i][c], k x m x W.
+// Runtime parity matrix P: column j as packed bits (PackedBits<W, M, 1>),
+// column_words(M, W) words per column.
 template <int W, int M>
-struct ColumnMasks {
+struct ColumnWords {
   const uint32_t* base;
-  __device__ __forceinline__ uint32_t bit(int j, int i, int c) const { return base[(j * M + i) * W + c]; }
+  struct Column {
+    const uint32_t* p;
+    __device__ __forceinline__ uint32_t word(int i) const { return p[i]; }
+  };
+  __device__ __forceinline__ Column column(int j) const { return Column{base + j * ((M * W + 31) / 32)}; }
 };
 
 // ------------------------------------------------------------------ bodies
-RS_CHD constexpr int body_warps(int regs_words) { return regs_words <= 64 ? 16 : 8; }
+RS_CHD constexpr int body_warps(int regs_words) { return regs_words <= 48 ? 16 : 8; }
+// Register budget: 8-warp GF(2^8) bodies whose live state (accumulators,
+// plus the outputs for a decode) is at most 64 words are compiled for two
+// resident CTAs per SM (about 113 registers), which they fit without
+// spilling; the others keep the one-CTA budget.
+RS_CHD constexpr int body_min_blocks(int w, int max_warps, int live_words) {
+  return (w == 8 && max_warps <= 8 && live_words <= 64) ? 2 : 1;
+}
 
 template <int W, int M, int OP>
 struct PolyBody {
   static constexpr int kW = W;
   static constexpr int kLayout = kLayoutSymbol;
   static constexpr int kMaxWarps = OP == kOpEncode ? body_warps(M * W) : 8;
+  static constexpr int kMinBlocks = body_min_blocks(W, kMaxWarps, (OP == kOpEncode ? 1 : 2) * M * W);
   __device__ static bool matches(const StripeDesc& d) { return d.op == OP && d.m == M; }
   template <class Tile>
   __device__ static void run(const StripeDesc& d, Tile& t, const uint32_t* coef) {
     if constexpr (OP == kOpEncode) {
       PolyEncode<W, M>::run((int)d.k, t, t);
     } else {
-      CoefMasks<W, M> cm{coef + d.coef_off};
+      CoefWords cm{coef + d.coef_off};
       PolyDecode<W, M>::run((int)d.n_pos, d.read_mask, (int)d.e, t, t, cm);
     }
   }
@@ -248,14 +263,15 @@ struct MatRuntimeBody {
   static constexpr int kW = W;
   static constexpr int kLayout = LAYOUT;
   static constexpr int kMaxWarps = 8;
+  static constexpr int kMinBlocks = body_min_blocks(W, kMaxWarps, (OP == kOpMatEncode ? 1 : 2) * M * W + 16);
   __device__ static bool matches(const StripeDesc& d) { return d.op == OP && d.m == M; }
   template <class Tile>
   __device__ static void run(const StripeDesc& d, Tile& t, const uint32_t* coef) {
-    ColumnMasks<W, M> cols{reinterpret_cast<const uint32_t*>(d.pmask)};
+    ColumnWords<W, M> cols{reinterpret_cast<const uint32_t*>(d.pmask)};
     if constexpr (OP == kOpMatEncode) {
       MatEncodeRuntime<W, M, LAYOUT == kLayoutSymbol>::run((int)d.k, t, t, cols);
     } else {
-      CoefMasks<W, M> cm{coef + d.coef_off};
+      CoefWords cm{coef + d.coef_off};
       MatDecodeRuntime<W, M, LAYOUT == kLayoutSymbol>::run((int)d.k, d.read_mask, (int)d.e, t, t, cols, cm);
     }
   }
@@ -266,13 +282,14 @@ struct MatFixedBody {
   static constexpr int kW = W;
   static constexpr int kLayout = KIND == kKindCauchy ? kLayoutPacket : kLayoutSymbol;
   static constexpr int kMaxWarps = 8;
+  static constexpr int kMinBlocks = body_min_blocks(W, kMaxWarps, (OP == kOpMatEncode ? 1 : 2) * M * W);
   __device__ static bool matches(const StripeDesc& d) { return d.op == OP && d.m == M && d.k == K; }
   template <class Tile>
   __device__ static void run(const StripeDesc& d, Tile& t, const uint32_t* coef) {
     if constexpr (OP == kOpMatEncode) {
       MatEncodeFixed<W, K, M, KIND, kLayout == kLayoutSymbol>::run(t, t);
     } else {
-      CoefMasks<W, M> cm{coef + d.coef_off};
+      CoefWords cm{coef + d.coef_off};
       MatDecodeFixed<W, K, M, KIND, kLayout == kLayoutSymbol>::run(d.read_mask, (int)d.e, t, t, cm);
     }
   }
@@ -290,6 +307,12 @@ struct MixedBody {
     return w;
   }
   static constexpr int kMaxWarps = min_warps();
+  static constexpr int min_blocks() {
+    int b = First::kMinBlocks;
+    ((b = Rest::kMinBlocks < b ? Rest::kMinBlocks : b), ...);
+    return b;
+  }
+  static constexpr int kMinBlocks = min_blocks();
   __device__ static bool matches(const StripeDesc& d) { return First::matches(d) || (Rest::matches(d) || ...); }
   template <class Tile>
   __device__ static void run(const StripeDesc& d, Tile& t, const uint32_t* coef) {
@@ -305,6 +328,7 @@ struct MixedBody {
 template <int W, int LAYOUT>
 __device__ __forceinline__ void producer_loop(const JobParams& p, const StripeDesc* stripes, const uint64_t* ptrs,
                                               Ring& ring, uint32_t n_stripes, uint32_t total_tiles) {
+  if (p.inject == kInjectProducerStall && blockIdx.x == 0) return;  // test hook, see job.hpp
   uint32_t q = 0;
   bool ok = true;
   for (uint32_t tile = blockIdx.x; tile < total_tiles && ok; tile += gridDim.x) {
@@ -313,7 +337,7 @@ __device__ __forceinline__ void producer_loop(const JobParams& p, const StripeDe
     const uint64_t* ip = ptrs + d.ptr_off;
     for (int i = 0; i < d.n_in; ++i) {
       const uint32_t s = ring.s, par = ring.par;
-      if (q >= ring.depth && !mbar_wait(&ring.empty[s], par ^ 1u)) {
+      if (q >= ring.depth && !mbar_wait(&ring.empty[s], par ^ 1u, p.wait_limit_ns)) {
         record_status(p.status, kDevErrTimeoutEmpty);
         ok = false;
         break;
@@ -342,16 +366,14 @@ __device__ __forceinline__ void producer_loop(const JobParams& p, const StripeDe
   // memory, so wait for the last fills to land (they complete on their own).
   const uint32_t first = q > ring.depth ? q - ring.depth : 0;
   for (uint32_t f = first; f < q; ++f) {
-    if (!mbar_wait(&ring.full[f % ring.depth], (f / ring.depth) & 1u)) {
+    if (!mbar_wait(&ring.full[f % ring.depth], (f / ring.depth) & 1u, p.wait_limit_ns))
       record_status(p.status, kDevErrTimeoutDrain);
-      break;
-    }
   }
 }
 
 // ------------------------------------------------------------------ kernel
 template <class Body>
-__global__ void __launch_bounds__((Body::kMaxWarps + 1) * 32, 1)
+__global__ void __launch_bounds__((Body::kMaxWarps + 1) * 32, Body::kMinBlocks)
     rs_stripe_kernel(const __grid_constant__ JobParams p) {
   constexpr int W = Body::kW;
   extern __shared__ __align__(128) uint8_t smem[];
@@ -387,6 +409,7 @@ __global__ void __launch_bounds__((Body::kMaxWarps + 1) * 32, 1)
   Tile tile;
   tile.ring = &ring;
   tile.status = p.status;
+  tile.limit = p.wait_limit_ns;
   tile.failed = false;
   if constexpr (Body::kLayout == kLayoutSymbol) {
     tile.lane = (uint32_t)lane;

@@ -64,6 +64,8 @@ def lib() -> ctypes.CDLL:
                 "rs_decode": (ctypes.c_int, [VP, ctypes.POINTER(ctypes.c_int), ctypes.c_int,
                                              ctypes.POINTER(VP), ctypes.c_size_t, VP]),
                 "rs_poll_status": (ctypes.c_int, [VP, ctypes.POINTER(ctypes.c_int)]),
+                "rs_set_wait_limit": (ctypes.c_int, [VP, ctypes.c_ulonglong]),
+                "rs_inject_fault": (ctypes.c_int, [VP, ctypes.c_int]),
                 "rs_batch_create": (ctypes.c_int, [ctypes.c_int, ctypes.POINTER(VP)]),
                 "rs_batch_destroy": (None, [VP]),
                 "rs_batch_set_launch": (ctypes.c_int, [VP, ctypes.c_int, ctypes.c_int, ctypes.c_int]),
@@ -145,6 +147,14 @@ def rs_encode(handle: int, data, parity, block_bytes: int, stream=None) -> None:
 def rs_decode(handle: int, erasures, blocks, block_bytes: int, stream=None) -> None:
     er = (ctypes.c_int * max(1, len(erasures)))(*erasures)
     _check(lib().rs_decode(handle, er, len(erasures), _ptr_array(blocks), block_bytes, _stream(stream)))
+
+
+def rs_set_wait_limit(handle: int, nanoseconds: int) -> None:
+    _check(lib().rs_set_wait_limit(handle, nanoseconds))
+
+
+def rs_inject_fault(handle: int, fault: int) -> None:
+    _check(lib().rs_inject_fault(handle, fault))
 
 
 def rs_poll_status(handle: int) -> int:

@@ -1,0 +1,363 @@
+"""Continuous-batching request server for RS encode/decode on one GPU.
+
+Requests (encode or decode of one stripe of some code and block size)
+arrive over time.  The loop:
+  - admits arrived requests while their stripe fits the device-memory
+    budget (a first-fit arena of pre-allocated device memory: buffers stay
+    resident and are reused, nothing is allocated per request);
+  - as soon as one of `streams` launch slots is free, packs every admitted
+    request into one batch (rs_batch_set + rs_batch_launch: one persistent
+    launch per kernel group) on that slot's stream, preceded by the
+    host->device copy of the request's input blocks and followed by the
+    device->host copy of its output blocks;
+  - polls the slots' completion events; a finished request frees its arena
+    memory, which admits the next arrivals.
+Requests arriving while earlier batches run are admitted and launched on
+another stream, so their transfers and kernels overlap on the device
+(continuous batching, not a queue drained one batch at a time).
+
+Latency of a request = host time of completion (its batch's event observed)
+- its arrival time.  The serial baseline runs every request alone
+(rs_encode / rs_decode, copies, synchronise) in arrival order.
+"""
+from __future__ import annotations
+
+import argparse
+import bisect
+import json
+import math
+import os
+import sys
+import time
+from dataclasses import dataclass, field
+
+import numpy as np
+
+from . import inputs
+
+CODES = [(6, 3), (10, 4), (12, 4), (20, 4)]
+ALIGN = 256
+
+
+# ----------------------------------------------------------------- arena
+class Arena:
+    """First-fit allocator over [0, capacity) with coalescing free list."""
+
+    def __init__(self, capacity: int):
+        self.capacity = capacity
+        self.free = [(0, capacity)]  # sorted (offset, size)
+        self.used = 0
+
+    def alloc(self, size: int):
+        size = (size + ALIGN - 1) // ALIGN * ALIGN
+        for i, (off, sz) in enumerate(self.free):
+            if sz >= size:
+                if sz == size:
+                    self.free.pop(i)
+                else:
+                    self.free[i] = (off + size, sz - size)
+                self.used += size
+                return off, size
+        return None
+
+    def release(self, off: int, size: int):
+        i = bisect.bisect_left(self.free, (off, 0))
+        self.free.insert(i, (off, size))
+        self.used -= size
+        # coalesce with neighbours
+        if i + 1 < len(self.free) and self.free[i][0] + self.free[i][1] == self.free[i + 1][0]:
+            self.free[i] = (self.free[i][0], self.free[i][1] + self.free[i + 1][1])
+            self.free.pop(i + 1)
+        if i > 0 and self.free[i - 1][0] + self.free[i - 1][1] == self.free[i][0]:
+            self.free[i - 1] = (self.free[i - 1][0], self.free[i - 1][1] + self.free[i][1])
+            self.free.pop(i)
+
+
+# --------------------------------------------------------------- requests
+@dataclass
+class Request:
+    rid: int
+    arrival: float          # seconds from the start of the run
+    k: int
+    m: int
+    op: str                 # "encode" / "decode"
+    block_bytes: int
+    erasures: list = field(default_factory=list)
+    payload: int = 0        # index of the host payload stripe
+    # filled by the server
+    admitted: float = -1.0
+    done: float = -1.0
+    off: int = -1
+    size: int = 0
+
+
+def make_requests(seed: int, rate: float, seconds: float, median: int = 256 << 10, sigma: float = 1.0,
+                  cap: int = 64 << 20, decode_frac: float = 0.25, max_requests: int | None = None):
+    """Poisson arrivals at `rate`/s for `seconds`; block sizes lognormal
+    (median, sigma) rounded down to 4 KiB, capped; codes uniform over CODES;
+    `decode_frac` decodes with e uniform in 1..m."""
+    n_max = max_requests or int(rate * seconds * 1.5 + 100)
+    u = inputs.uniform01(inputs.shape_draws(seed, 0, 6 * n_max)).reshape(n_max, 6)
+    t = 0.0
+    out = []
+    for i in range(n_max):
+        t += -math.log(1.0 - u[i, 0]) / rate
+        if t > seconds:
+            break
+        k, m = CODES[int(u[i, 1] * len(CODES)) % len(CODES)]
+        # Box-Muller from two uniforms for the lognormal size
+        z = math.sqrt(-2.0 * math.log(1.0 - u[i, 2])) * math.cos(2.0 * math.pi * u[i, 3])
+        B = int(median * math.exp(sigma * z))
+        B = max(4096, min(cap, B // 4096 * 4096))
+        op = "decode" if u[i, 4] < decode_frac else "encode"
+        er = []
+        if op == "decode":
+            e = 1 + int(u[i, 5] * m) % m
+            er = inputs.erasure_pattern(seed, i, k + m, e)
+        out.append(Request(rid=i, arrival=t, k=k, m=m, op=op, block_bytes=B, erasures=er))
+    return out
+
+
+def io_blocks(req: Request):
+    """(blocks copied host->device, blocks copied device->host)."""
+    n = req.k + req.m
+    if req.op == "encode":
+        return list(range(req.k)), list(range(req.k, n))
+    read = [b for b in range(n) if b not in req.erasures][:req.k]
+    return read, list(req.erasures)
+
+
+def algorithmic_bytes(req: Request) -> int:
+    if req.op == "encode":
+        return (req.k + req.m) * req.block_bytes
+    return (req.k + len(req.erasures)) * req.block_bytes
+
+
+# ----------------------------------------------------------------- server
+class Server:
+    def __init__(self, budget_bytes: int, streams: int = 4, max_batch: int = 256, device=None):
+        import torch
+
+        from . import rs
+
+        self.torch, self.rs = torch, rs
+        self.device = device or torch.device("cuda", torch.cuda.current_device())
+        self.budget = budget_bytes
+        self.arena = Arena(budget_bytes)
+        self.mem = torch.empty(budget_bytes, dtype=torch.uint8, device=self.device)
+        self.base = self.mem.data_ptr()
+        self.codes = {}
+        for (k, m) in CODES:
+            self.codes[(k, m)] = rs.Code(k, m, 8, "poly")
+        self.max_batch = max_batch
+        self.slots = []
+        for _ in range(streams):
+            self.slots.append({"stream": torch.cuda.Stream(device=self.device),
+                               "batch": rs.Batch(max_batch), "event": torch.cuda.Event(),
+                               "reqs": None})
+
+    def _block_view(self, off: int, b: int, B: int):
+        start = off + b * ((B + 15) // 16 * 16)
+        return self.mem[start:start + B]
+
+    def run(self, requests, payloads, results=None, time_limit: float | None = None):
+        """Serve `requests` (sorted by arrival) in real time.  payloads[i] is a
+        pinned uint8 host tensor (n, B) holding the stripe of request i (for
+        decodes: the codeword with erased blocks ignored); results[i], when
+        given, receives the output blocks (pinned host tensor (n_out, B))."""
+        torch = self.torch
+        pending = list(requests)
+        admitted = []
+        pi = 0
+        t0 = time.perf_counter()
+        done = 0
+        while done < len(requests):
+            now = time.perf_counter() - t0
+            if time_limit and now > time_limit:
+                break
+            # 1. admit arrivals that fit the budget (in arrival order)
+            while pi < len(pending) and pending[pi].arrival <= now:
+                r = pending[pi]
+                n = r.k + r.m
+                need = n * ((r.block_bytes + 15) // 16 * 16)
+                if need > self.budget:
+                    raise ValueError(f"request {r.rid} needs more than the whole budget")
+                got = self.arena.alloc(need)
+                if got is None:
+                    break
+                r.off, r.size = got
+                r.admitted = now
+                admitted.append(r)
+                pi += 1
+            # 2. launch admitted requests on a free slot
+            if admitted:
+                for slot in self.slots:
+                    if slot["reqs"] is None:
+                        batch_reqs = admitted[:self.max_batch]
+                        admitted = admitted[self.max_batch:]
+                        self._launch(slot, batch_reqs, payloads, results)
+                        break
+            # 3. retire finished slots
+            for slot in self.slots:
+                if slot["reqs"] is not None and slot["event"].query():
+                    tdone = time.perf_counter() - t0
+                    for r in slot["reqs"]:
+                        r.done = tdone
+                        self.arena.release(r.off, r.size)
+                        done += 1
+                    slot["reqs"] = None
+            if not admitted and (pi >= len(pending) or pending[pi].arrival > time.perf_counter() - t0):
+                busy = any(s["reqs"] is not None for s in self.slots)
+                if not busy and pi < len(pending):
+                    # idle until the next arrival
+                    wait = pending[pi].arrival - (time.perf_counter() - t0)
+                    if wait > 0:
+                        time.sleep(min(wait, 0.001))
+        return requests
+
+    def _launch(self, slot, reqs, payloads, results):
+        torch = self.torch
+        st = slot["stream"]
+        ops = []
+        with torch.cuda.stream(st):
+            for r in reqs:
+                n, B = r.k + r.m, r.block_bytes
+                blocks = [self._block_view(r.off, b, B) for b in range(n)]
+                h2d, _ = io_blocks(r)
+                for b in h2d:
+                    blocks[b].copy_(payloads[r.rid][b], non_blocking=True)
+                ops.append((self.codes[(r.k, r.m)], r.op, r.erasures, blocks, B))
+            slot["batch"].set(ops, stream=st)
+            slot["batch"].launch(stream=st)
+            if results is not None:
+                for r in reqs:
+                    _, d2h = io_blocks(r)
+                    for j, b in enumerate(d2h):
+                        results[r.rid][j].copy_(self._block_view(r.off, b, r.block_bytes), non_blocking=True)
+            slot["event"].record(st)
+        slot["reqs"] = reqs
+
+
+def serial_run(requests, payloads, results, codes, device):
+    """Every request alone, in arrival order (copies, one launch, sync)."""
+    import torch
+    t0 = time.perf_counter()
+    bufs = {}
+    for r in requests:
+        now = time.perf_counter() - t0
+        if r.arrival > now:
+            time.sleep(r.arrival - now)
+        n, B = r.k + r.m, r.block_bytes
+        key = (n, B)
+        if key not in bufs:
+            bufs[key] = torch.empty((n, (B + 15) // 16 * 16), dtype=torch.uint8, device=device)
+        buf = bufs[key]
+        blocks = [buf[b, :B] for b in range(n)]
+        h2d, d2h = io_blocks(r)
+        for b in h2d:
+            blocks[b].copy_(payloads[r.rid][b], non_blocking=True)
+        code = codes[(r.k, r.m)]
+        if r.op == "encode":
+            code.encode(blocks[:r.k], blocks[r.k:], B)
+        else:
+            code.decode(r.erasures, blocks, B)
+        for j, b in enumerate(d2h):
+            results[r.rid][j].copy_(blocks[b], non_blocking=True)
+        torch.cuda.synchronize()
+        r.done = time.perf_counter() - t0
+    return requests
+
+
+def summarize(requests, wall: float | None = None):
+    lat = np.array([r.done - r.arrival for r in requests if r.done >= 0])
+    done = [r for r in requests if r.done >= 0]
+    if not len(lat):
+        return {"completed": 0}
+    span = wall or (max(r.done for r in done) - min(r.arrival for r in done))
+    return {"completed": len(done), "p50_ms": float(np.percentile(lat, 50) * 1e3),
+            "p99_ms": float(np.percentile(lat, 99) * 1e3),
+            "gbs": sum(algorithmic_bytes(r) for r in done) / span / 1e9, "span_s": span}
+
+
+def make_payloads(requests, pool: int = 32):
+    """Pinned host stripes for the requests: a pool of seeded random encoded
+    stripes per (code, block size) shape, shared between requests of that
+    shape (content is irrelevant to timing; tests use distinct stripes)."""
+    import torch
+    from . import rs
+    shapes = {}
+    out = {}
+    for r in requests:
+        key = (r.k, r.m, r.block_bytes)
+        shapes.setdefault(key, []).append(r)
+    for (k, m, B), rs_ in shapes.items():
+        n = k + m
+        cnt = min(pool, len(rs_))
+        host = torch.empty((cnt, n, B), dtype=torch.uint8).pin_memory()
+        dev = torch.empty((cnt, n, (B + 15) // 16 * 16), dtype=torch.uint8, device="cuda")
+        seed = inputs.config_seed(5)
+        dev[:, :k, :B] = inputs.random_bytes_torch(seed ^ (k * 131 + B), 0, cnt * k * B, "cuda").view(cnt, k, B)
+        code = rs.Code(k, m, 8, "poly")
+        for i in range(cnt):
+            rows = [dev[i, b, :B] for b in range(n)]
+            code.encode(rows[:k], rows[k:], B)
+        torch.cuda.synchronize()
+        host.copy_(dev[:, :, :B].cpu())
+        for i, r in enumerate(rs_):
+            out[r.rid] = host[i % cnt]
+        del dev
+    return out
+
+
+def make_results(requests):
+    import torch
+    return {r.rid: torch.empty((len(io_blocks(r)[1]), r.block_bytes), dtype=torch.uint8).pin_memory()
+            for r in requests}
+
+
+def saturation_rate(budget: int, seconds: float = 2.0, seed: int = 0x5EED0005) -> float:
+    """Requests/s the batched server sustains when every request is already
+    waiting (all arrivals at t = 0)."""
+    reqs = make_requests(seed, 1e9, 1.0, max_requests=int(400 * seconds))
+    for r in reqs:
+        r.arrival = 0.0
+    payloads = make_payloads(reqs)
+    srv = Server(budget)
+    t0 = time.perf_counter()
+    srv.run(reqs, payloads)
+    dt = time.perf_counter() - t0
+    return len(reqs) / dt
+
+
+def main():
+    ap = argparse.ArgumentParser(description=__doc__, formatter_class=argparse.RawDescriptionHelpFormatter)
+    ap.add_argument("--budget-gib", type=float, default=32.0)
+    ap.add_argument("--seconds", type=float, default=60.0)
+    ap.add_argument("--rates", default="0.1,0.5,0.9,1.2", help="fractions of the saturation rate")
+    ap.add_argument("--streams", type=int, default=4)
+    ap.add_argument("--serial", action="store_true", help="also run the serial per-request path")
+    a = ap.parse_args()
+    budget = int(a.budget_gib * (1 << 30))
+    sat = saturation_rate(budget)
+    out = {"saturation_req_per_s": sat, "runs": []}
+    for frac in [float(x) for x in a.rates.split(",")]:
+        rate = frac * sat
+        reqs = make_requests(inputs.config_seed(5), rate, a.seconds)
+        payloads = make_payloads(reqs)
+        results = make_results(reqs)
+        Server(budget, streams=a.streams).run(reqs, payloads, results)
+        row = {"rate_frac": frac, "rate": rate, "batched": summarize(reqs)}
+        if a.serial:
+            import torch
+            from . import rs
+            codes = {c: rs.Code(c[0], c[1], 8, "poly") for c in CODES}
+            reqs2 = make_requests(inputs.config_seed(5), rate, a.seconds)
+            serial_run(reqs2, payloads, results, codes, torch.device("cuda"))
+            row["serial"] = summarize(reqs2)
+        out["runs"].append(row)
+        print(json.dumps(row), flush=True)
+    print(json.dumps(out))
+
+
+if __name__ == "__main__":
+    main()

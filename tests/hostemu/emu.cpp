@@ -45,10 +45,10 @@ struct HostTile {
   }
 };
 
-template <int W, int M>
 struct HostCoef {
-  const DecodePlan* pl;
-  uint32_t bit(int t, int j, int c) const { return (pl->W[t][j] >> c) & 1u; }
+  std::vector<uint32_t> words;
+  explicit HostCoef(const DecodePlan* pl, int w) : words(pack_decode_matrix(*pl, w)) {}
+  uint32_t word(int i) const { return words[i]; }
 };
 
 template <int W, int M>
@@ -72,7 +72,7 @@ void run_decode(const DecodePlan& pl, uint8_t* blocks, size_t B) {
   for (int b : pl.in_blocks) in.push_back(blocks + (size_t)b * B);
   for (int b : pl.out_blocks) out.push_back(blocks + (size_t)b * B);
   const size_t segb = segment_bytes(W);
-  HostCoef<W, M> cf{&pl};
+  HostCoef cf(&pl, W);
   for (size_t seg = 0; seg < B; seg += segb)
     for (int lane = 0; lane < 32; ++lane) {
       HostTile<W> t{in.data(), out.data(), B, seg, lane};
@@ -135,9 +135,13 @@ struct HostPacketTile {
 
 template <int W, int M>
 struct HostCols {
-  const std::vector<uint32_t>* P;
-  int k;
-  uint32_t bit(int j, int i, int c) const { return ((*P)[(size_t)i * k + j] >> c) & 1u; }
+  std::vector<uint32_t> words;
+  HostCols(const std::vector<uint32_t>& P, int k) : words(pack_columns(P, k, M, W)) {}
+  struct Column {
+    const uint32_t* p;
+    uint32_t word(int i) const { return p[i]; }
+  };
+  Column column(int j) const { return Column{words.data() + (size_t)j * column_words(M, W)}; }
 };
 
 // Runs `body(tile)` over every 32-column group of the stripe in the layout.
@@ -164,7 +168,7 @@ int mat_runtime(int k, const std::vector<uint32_t>& P, bool decode, const Decode
                 size_t pkt) {
   std::vector<const uint8_t*> in;
   std::vector<uint8_t*> out;
-  HostCols<W, M> cols{&P, k};
+  HostCols<W, M> cols(P, k);
   if (!decode) {
     for (int j = 0; j < k; ++j) in.push_back(blocks + (size_t)j * B);
     for (int i = 0; i < M; ++i) out.push_back(blocks + (size_t)(k + i) * B);
@@ -172,7 +176,7 @@ int mat_runtime(int k, const std::vector<uint32_t>& P, bool decode, const Decode
   } else {
     for (int b : pl->in_blocks) in.push_back(blocks + (size_t)b * B);
     for (int b : pl->out_blocks) out.push_back(blocks + (size_t)b * B);
-    HostCoef<W, M> cf{pl};
+    HostCoef cf(pl, W);
     for_groups<W, kPacket>(in, out, B, pkt, [&](auto& t) {
       MatDecodeRuntime<W, M, !kPacket>::run(k, pl->read_mask, pl->e, t, t, cols, cf);
     });
@@ -192,7 +196,7 @@ int mat_fixed(bool decode, const DecodePlan* pl, uint8_t* blocks, size_t B, size
   } else {
     for (int b : pl->in_blocks) in.push_back(blocks + (size_t)b * B);
     for (int b : pl->out_blocks) out.push_back(blocks + (size_t)b * B);
-    HostCoef<W, M> cf{pl};
+    HostCoef cf(pl, W);
     for_groups<W, kPacket>(in, out, B, pkt, [&](auto& t) {
       MatDecodeFixed<W, K, M, KIND, !kPacket>::run(pl->read_mask, pl->e, t, t, cf);
     });
