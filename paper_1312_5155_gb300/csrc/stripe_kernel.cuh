@@ -119,7 +119,18 @@ struct SymTile {
     len = g.len;
   }
 
+  // Inputs are consumed in order 0..n_in-1; load(i) hands out input i
+  // (fetched while step i-1 was computing) and starts fetching input i+1,
+  // so the slot wait and shared-memory latency overlap the arithmetic.
+  uint32_t nxt[W];
   __device__ __forceinline__ void load(int i, uint32_t* x) {
+    if (i == 0) fetch(0, nxt);
+#pragma unroll
+    for (int b = 0; b < W; ++b) x[b] = nxt[b];
+    if (i + 1 < n_in) fetch(i + 1, nxt);
+  }
+
+  __device__ __forceinline__ void fetch(int i, uint32_t* x) {
     Ring& r = *ring;
     const uint32_t s = r.s, par = r.par;
     r.advance();
@@ -192,7 +203,15 @@ struct PacketTile {
     P = d.packet_bytes;
   }
 
+  uint32_t nxt[W];
   __device__ __forceinline__ void load(int i, uint32_t* x) {
+    if (i == 0) fetch(0, nxt);
+#pragma unroll
+    for (int b = 0; b < W; ++b) x[b] = nxt[b];
+    if (i + 1 < n_in) fetch(i + 1, nxt);
+  }
+
+  __device__ __forceinline__ void fetch(int i, uint32_t* x) {
     Ring& r = *ring;
     const uint32_t s = r.s, par = r.par;
     r.advance();
@@ -262,7 +281,7 @@ template <int W, int M, int OP, int LAYOUT>
 struct MatRuntimeBody {
   static constexpr int kW = W;
   static constexpr int kLayout = LAYOUT;
-  static constexpr int kMaxWarps = 8;
+  static constexpr int kMaxWarps = OP == kOpMatEncode ? body_warps(M * W + 16) : 8;
   static constexpr int kMinBlocks = body_min_blocks(W, kMaxWarps, (OP == kOpMatEncode ? 1 : 2) * M * W + 16);
   __device__ static bool matches(const StripeDesc& d) { return d.op == OP && d.m == M; }
   template <class Tile>
@@ -281,7 +300,7 @@ template <int W, int K, int M, int KIND, int OP>
 struct MatFixedBody {
   static constexpr int kW = W;
   static constexpr int kLayout = KIND == kKindCauchy ? kLayoutPacket : kLayoutSymbol;
-  static constexpr int kMaxWarps = 8;
+  static constexpr int kMaxWarps = OP == kOpMatEncode ? body_warps(M * W) : 8;
   static constexpr int kMinBlocks = body_min_blocks(W, kMaxWarps, (OP == kOpMatEncode ? 1 : 2) * M * W);
   __device__ static bool matches(const StripeDesc& d) { return d.op == OP && d.m == M && d.k == K; }
   template <class Tile>

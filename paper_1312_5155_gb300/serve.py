@@ -279,53 +279,54 @@ def summarize(requests, wall: float | None = None):
             "gbs": sum(algorithmic_bytes(r) for r in done) / span / 1e9, "span_s": span}
 
 
-def make_payloads(requests, pool: int = 32):
-    """Pinned host stripes for the requests: a pool of seeded random encoded
-    stripes per (code, block size) shape, shared between requests of that
-    shape (content is irrelevant to timing; tests use distinct stripes)."""
+class HostPool:
+    """One pinned host buffer of seeded random bytes; every request's payload
+    (and result) is a view into it.  Content is irrelevant to timing; the
+    correctness tests build their own per-request payloads."""
+
+    def __init__(self, nbytes: int, seed: int = 0x5EED0005):
+        import torch
+        self.buf = torch.empty(nbytes, dtype=torch.uint8).pin_memory()
+        chunk = min(nbytes, 64 << 20)
+        pattern = torch.from_numpy(inputs.random_bytes(seed, 0, chunk))
+        for off in range(0, nbytes, chunk):
+            n = min(chunk, nbytes - off)
+            self.buf[off:off + n].copy_(pattern[:n])
+        self.nbytes = nbytes
+
+    def view(self, rid: int, rows: int, cols: int):
+        need = rows * cols
+        if need > self.nbytes:
+            raise ValueError("pool smaller than one request")
+        off = (rid * 7919 * 4096) % (self.nbytes - need + 1) // 16 * 16
+        return self.buf[off:off + need].view(rows, cols)
+
+
+def make_payloads(requests, pool: "HostPool"):
+    return {r.rid: pool.view(r.rid, r.k + r.m, r.block_bytes) for r in requests}
+
+
+def make_results(requests, pool: "HostPool | None" = None):
     import torch
-    from . import rs
-    shapes = {}
-    out = {}
-    for r in requests:
-        key = (r.k, r.m, r.block_bytes)
-        shapes.setdefault(key, []).append(r)
-    for (k, m, B), rs_ in shapes.items():
-        n = k + m
-        cnt = min(pool, len(rs_))
-        host = torch.empty((cnt, n, B), dtype=torch.uint8).pin_memory()
-        dev = torch.empty((cnt, n, (B + 15) // 16 * 16), dtype=torch.uint8, device="cuda")
-        seed = inputs.config_seed(5)
-        dev[:, :k, :B] = inputs.random_bytes_torch(seed ^ (k * 131 + B), 0, cnt * k * B, "cuda").view(cnt, k, B)
-        code = rs.Code(k, m, 8, "poly")
-        for i in range(cnt):
-            rows = [dev[i, b, :B] for b in range(n)]
-            code.encode(rows[:k], rows[k:], B)
-        torch.cuda.synchronize()
-        host.copy_(dev[:, :, :B].cpu())
-        for i, r in enumerate(rs_):
-            out[r.rid] = host[i % cnt]
-        del dev
-    return out
+    if pool is None:
+        return {r.rid: torch.empty((len(io_blocks(r)[1]), r.block_bytes), dtype=torch.uint8).pin_memory()
+                for r in requests}
+    return {r.rid: pool.view(r.rid + 1, len(io_blocks(r)[1]), r.block_bytes) for r in requests}
 
 
-def make_results(requests):
-    import torch
-    return {r.rid: torch.empty((len(io_blocks(r)[1]), r.block_bytes), dtype=torch.uint8).pin_memory()
-            for r in requests}
-
-
-def saturation_rate(budget: int, seconds: float = 2.0, seed: int = 0x5EED0005) -> float:
+def saturation_rate(budget: int, pool: "HostPool", seconds: float = 2.0, seed: int = 0x5EED0005) -> float:
     """Requests/s the batched server sustains when every request is already
     waiting (all arrivals at t = 0)."""
     reqs = make_requests(seed, 1e9, 1.0, max_requests=int(400 * seconds))
     for r in reqs:
         r.arrival = 0.0
-    payloads = make_payloads(reqs)
+    payloads = make_payloads(reqs, pool)
     srv = Server(budget)
+    srv.run(reqs[:50], payloads)  # warm-up
     t0 = time.perf_counter()
     srv.run(reqs, payloads)
     dt = time.perf_counter() - t0
+    del srv
     return len(reqs) / dt
 
 
@@ -338,14 +339,16 @@ def main():
     ap.add_argument("--serial", action="store_true", help="also run the serial per-request path")
     a = ap.parse_args()
     budget = int(a.budget_gib * (1 << 30))
-    sat = saturation_rate(budget)
+    pool = HostPool(2 << 30)
+    sat = saturation_rate(budget, pool)
     out = {"saturation_req_per_s": sat, "runs": []}
+    srv = Server(budget, streams=a.streams)
     for frac in [float(x) for x in a.rates.split(",")]:
         rate = frac * sat
         reqs = make_requests(inputs.config_seed(5), rate, a.seconds)
-        payloads = make_payloads(reqs)
-        results = make_results(reqs)
-        Server(budget, streams=a.streams).run(reqs, payloads, results)
+        payloads = make_payloads(reqs, pool)
+        results = make_results(reqs, pool)
+        srv.run(reqs, payloads, results)
         row = {"rate_frac": frac, "rate": rate, "batched": summarize(reqs)}
         if a.serial:
             import torch
