@@ -186,6 +186,40 @@ int rs_batch_kernel_count(const rs_batch *batch);
 /* Read and clear the batch's device status word (as rs_poll_status). */
 rs_status rs_batch_poll_status(rs_batch *batch, int *device_status);
 
+/* ------------------------------------------------------------------------
+ * Allocation-free batched encode.  The paper has no counterpart: this entry
+ * point exists for callers that cannot allocate device memory when they
+ * encode -- code running while a stream is captured into a CUDA graph
+ * (cudaMalloc is not allowed there), allocator or memory-pool callbacks that
+ * must not re-enter the allocator, and embedders that own the whole device
+ * memory budget.  rs_init and rs_batch_create allocate (status word,
+ * descriptor tables); this call does not: all scratch the batched kernel
+ * needs (descriptor tables, pointer table, status word) lives in one
+ * fixed 256 KiB static device array, reserved on every GPU that loads the
+ * library until the process exits.  The caller passes only the blocks.
+ *
+ * Encodes n_stripes stripes of the polynomial RS(k, m) code over GF(2^w)
+ * (§3.2 Eq. 1 per stripe) in one persistent launch on `stream`:
+ *   data_ptrs:   n_stripes * k device pointers, stripe-major (stripe s uses
+ *                data_ptrs[s*k .. s*k+k-1]);
+ *   parity_ptrs: n_stripes * m device pointers, stripe-major;
+ *   block_bytes: n_stripes block sizes (0 skips the stripe).
+ * Block rules as for rs_encode.  Limits: those of rs_init, and the tables
+ * must fit the array: 256 + (n_stripes * 56 rounded up to 256) + n_stripes *
+ * (k + m) * 8 bytes <= 262144 (e.g. up to 1500 stripes of RS(10,4)); larger
+ * requests return RS_EINVAL with the sizes in rs_last_error.
+ * The first call on a device does a one-time set-up with that device
+ * current (the device address of the array, the kernel's shared-memory
+ * attribute); make that first call before any stream capture.  The array is
+ * shared by all calls on a device and keeps the last call's contents: the
+ * status word is cleared at the start of each call and the tables are
+ * rewritten, so calls whose work overlaps on the GPU race -- order them on
+ * one stream or synchronise between them.  Device-side wait timeouts are
+ * recorded in the array's status word only (not reported to the caller).
+ * Errors: RS_EINVAL, RS_EUNSUPPORTED, RS_ECUDA. */
+rs_status rs_poly_encode_stripes_noalloc(int k, int m, int w, int n_stripes, const void *const *data_ptrs,
+                                         void *const *parity_ptrs, const size_t *block_bytes, void *stream);
+
 #ifdef __cplusplus
 }
 #endif

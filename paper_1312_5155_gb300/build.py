@@ -125,7 +125,8 @@ def generate_units() -> list[str]:
 
 
 def sources() -> list[str]:
-    return [os.path.join(CSRC, "capi.cu"), os.path.join(CSRC, "plan.cpp")] + generate_units()
+    return [os.path.join(CSRC, "capi.cu"), os.path.join(CSRC, "plan.cpp"),
+            os.path.join(CSRC, "noalloc.cu")] + generate_units()
 
 
 def _obj(src: str) -> str:

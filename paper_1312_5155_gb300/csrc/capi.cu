@@ -54,6 +54,11 @@ bool has_fixed_kernels(int w, int k, int m) {
 
 }  // namespace
 
+namespace rsgb {
+void set_last_error(const std::string& msg) { g_last_error = msg; }
+void clear_last_error() { g_last_error.clear(); }
+}  // namespace rsgb
+
 struct rs_code {
   int k = 0, m = 0, w = 0;
   Realization real = Realization::Poly;

@@ -3,6 +3,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <string>
+
 #include "job.hpp"
 
 namespace rsgb {
@@ -21,6 +23,11 @@ struct TuneCfg {
   int depth = 16;          // ring slots
   int ctas_per_sm = 1;
 };
+
+// Thread-local message behind rs_last_error (set on failure, cleared on
+// success by every entry point).
+void set_last_error(const std::string& msg);
+void clear_last_error();
 
 inline size_t ring_smem_bytes(uint32_t depth, uint32_t slice) {
   return ((2u * depth * 8u + 127u) & ~127u) + (size_t)depth * slice;

@@ -66,6 +66,10 @@ def lib() -> ctypes.CDLL:
                 "rs_poll_status": (ctypes.c_int, [VP, ctypes.POINTER(ctypes.c_int)]),
                 "rs_set_wait_limit": (ctypes.c_int, [VP, ctypes.c_ulonglong]),
                 "rs_inject_fault": (ctypes.c_int, [VP, ctypes.c_int]),
+                "rs_poly_encode_stripes_noalloc": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                                                                   ctypes.c_int, ctypes.POINTER(VP),
+                                                                   ctypes.POINTER(VP),
+                                                                   ctypes.POINTER(ctypes.c_size_t), VP]),
                 "rs_batch_create": (ctypes.c_int, [ctypes.c_int, ctypes.POINTER(VP)]),
                 "rs_batch_destroy": (None, [VP]),
                 "rs_batch_set_launch": (ctypes.c_int, [VP, ctypes.c_int, ctypes.c_int, ctypes.c_int]),
@@ -242,11 +246,10 @@ def make_ops(ops):
         o.n_erasures = len(er)
         for j, x in enumerate(er):
             o.erasures[j] = x
-        blocks = list(blocks)
-        if len(blocks) > 64:
+        ptrs = [b if isinstance(b, int) else _ptr(b) for b in blocks]
+        if len(ptrs) > 64:
             raise ValueError("at most 64 blocks")
-        for j, b in enumerate(blocks):
-            o.blocks[j] = _ptr(b)
+        o.blocks[:len(ptrs)] = ptrs
         o.block_bytes = nbytes
     return arr, len(ops)
 
@@ -309,3 +312,18 @@ class Batch:
             self.close()
         except Exception:
             pass
+
+
+# ------------------------------------------------- allocation-free encode
+def rs_poly_encode_stripes_noalloc(k: int, m: int, w: int, data, parity, block_bytes, stream=None) -> None:
+    """Encode several polynomial RS(k, m) stripes without any device
+    allocation (for callers that cannot allocate: graph capture, allocator
+    callbacks, fixed memory budgets).  data: per stripe k device blocks;
+    parity: per stripe m device blocks; block_bytes: per stripe sizes."""
+    n = len(block_bytes)
+    if len(data) != n or len(parity) != n:
+        raise ValueError("data, parity and block_bytes need one entry per stripe")
+    dp = _ptr_array([b for stripe in data for b in stripe])
+    pp = _ptr_array([b for stripe in parity for b in stripe])
+    bb = (ctypes.c_size_t * max(1, n))(*block_bytes)
+    _check(lib().rs_poly_encode_stripes_noalloc(k, m, w, n, dp, pp, bb, _stream(stream)))
