@@ -67,6 +67,11 @@ def lib():
                                       ctypes.c_size_t],
                 "rso_cauchy_decode": [ctypes.c_int, ctypes.c_int, ctypes.c_int, IP, ctypes.c_int, U8P,
                                       ctypes.c_size_t, ctypes.c_size_t],
+                "rso_polymat_matrix": [ctypes.c_int, ctypes.c_int, ctypes.c_int, U32P],
+                "rso_polybm_encode": [ctypes.c_int, ctypes.c_int, ctypes.c_int, U8P, ctypes.c_size_t,
+                                      ctypes.c_size_t],
+                "rso_polybm_decode": [ctypes.c_int, ctypes.c_int, ctypes.c_int, IP, ctypes.c_int, U8P,
+                                      ctypes.c_size_t, ctypes.c_size_t],
             }.items():
                 fn = getattr(L, name)
                 fn.argtypes = args
@@ -217,10 +222,33 @@ def cauchy_decode(w: int, k: int, m: int, erasures, blocks: np.ndarray, packet_b
     return b
 
 
+# ------------------------------------- polynomial code as a generator matrix
+def polymat_matrix(w: int, k: int, m: int) -> np.ndarray:
+    Pm = np.zeros(m * k, dtype=np.uint32)
+    _check(lib().rso_polymat_matrix(w, k, m, _p32(Pm)), "polymat_matrix")
+    return Pm.reshape(m, k)
+
+
+def polybm_encode(w: int, k: int, m: int, blocks: np.ndarray, packet_bytes: int) -> np.ndarray:
+    b = _blocks(blocks, k + m)
+    _check(lib().rso_polybm_encode(w, k, m, b.ctypes.data_as(U8P), b.shape[1], packet_bytes), "polybm_encode")
+    return b
+
+
+def polybm_decode(w: int, k: int, m: int, erasures, blocks: np.ndarray, packet_bytes: int) -> np.ndarray:
+    b = _blocks(blocks, k + m)
+    er = np.ascontiguousarray(np.asarray(erasures, dtype=np.int32))
+    _check(lib().rso_polybm_decode(w, k, m, er.ctypes.data_as(IP), er.size, b.ctypes.data_as(U8P),
+                                   b.shape[1], packet_bytes), "polybm_decode")
+    return b
+
+
 # ------------------------------------------------------ generic dispatch
 def encode(realization: str, w: int, k: int, m: int, blocks: np.ndarray, packet_bytes: int = 2048):
-    if realization == "poly":
+    if realization in ("poly", "poly_matrix"):
         return poly_encode(w, k, m, blocks)
+    if realization == "poly_bitmatrix":
+        return polybm_encode(w, k, m, blocks, packet_bytes)
     if realization == "vandermonde":
         return vand_encode(w, k, m, blocks)
     if realization == "cauchy":
@@ -230,8 +258,10 @@ def encode(realization: str, w: int, k: int, m: int, blocks: np.ndarray, packet_
 
 def decode(realization: str, w: int, k: int, m: int, erasures, blocks: np.ndarray,
            packet_bytes: int = 2048):
-    if realization == "poly":
+    if realization in ("poly", "poly_matrix"):
         return poly_decode(w, k, m, erasures, blocks)
+    if realization == "poly_bitmatrix":
+        return polybm_decode(w, k, m, erasures, blocks, packet_bytes)
     if realization == "vandermonde":
         return vand_decode(w, k, m, erasures, blocks)
     if realization == "cauchy":

@@ -510,28 +510,35 @@ static int cauchy_check(int w, int k, int m, size_t B, size_t P, field_t **f) {
     return 0;
 }
 
+/* Encode with the bit-matrix projection of an m x k parity matrix C. */
+static int bitmatrix_code_encode(const field_t *f, int w, int k, int m, const uint32_t *C, uint8_t *blocks,
+                                 size_t B, size_t P) {
+    int *ins = (int *)malloc(sizeof(int) * (size_t)k);
+    if (!ins) return -3;
+    for (int j = 0; j < k; j++) ins[j] = j;
+    for (int i = 0; i < m; i++) bitmatrix_apply(f, w, k, ins, C + (size_t)i * k, blocks, B, P, k + i);
+    free(ins);
+    return 0;
+}
+
 int rso_cauchy_encode(int w, int k, int m, uint8_t *blocks, size_t B, size_t P) {
     field_t *f;
     if (cauchy_check(w, k, m, B, P, &f)) return -1;
     uint32_t *C = (uint32_t *)malloc(sizeof(uint32_t) * (size_t)m * k);
-    int *ins = (int *)malloc(sizeof(int) * (size_t)k);
-    if (!C || !ins) { free(C); free(ins); return -3; }
+    if (!C) return -3;
     rso_cauchy_matrix(w, k, m, C);
-    for (int j = 0; j < k; j++) ins[j] = j;
-    for (int i = 0; i < m; i++) bitmatrix_apply(f, w, k, ins, C + (size_t)i * k, blocks, B, P, k + i);
-    free(C); free(ins);
-    return 0;
+    int rc = bitmatrix_code_encode(f, w, k, m, C, blocks, B, P);
+    free(C);
+    return rc;
 }
 
 /* Decoding (§2.1 steps on the generator [I_k; C]): k survivors with the
  * lowest block indices, invert their k x k rows, project each needed row of
  * the inverse to bit-matrices and XOR the surviving packets; erased parity
  * is then re-encoded from the completed data. */
-int rso_cauchy_decode(int w, int k, int m, const int *er, int e, uint8_t *blocks, size_t B, size_t P) {
-    field_t *f;
-    if (cauchy_check(w, k, m, B, P, &f)) return -1;
+static int bitmatrix_code_decode(const field_t *f, int w, int k, int m, const uint32_t *Cin, const int *er,
+                                 int e, uint8_t *blocks, size_t B, size_t P) {
     int n = k + m;
-    if (check_erasures(n, m, er, e)) return -1;
     if (e == 0) return 0;
     uint32_t *C = (uint32_t *)malloc(sizeof(uint32_t) * (size_t)m * k);
     uint32_t *Gs = (uint32_t *)malloc(sizeof(uint32_t) * (size_t)k * k);
@@ -539,7 +546,7 @@ int rso_cauchy_decode(int w, int k, int m, const int *er, int e, uint8_t *blocks
     int *surv = (int *)malloc(sizeof(int) * (size_t)n);
     int *dat = (int *)malloc(sizeof(int) * (size_t)k);
     if (!C || !Gs || !Gi || !surv || !dat) { free(C); free(Gs); free(Gi); free(surv); free(dat); return -3; }
-    rso_cauchy_matrix(w, k, m, C);
+    memcpy(C, Cin, sizeof(uint32_t) * (size_t)m * k);
     char erased[512];
     memset(erased, 0, sizeof(erased));
     for (int t = 0; t < e; t++) erased[er[t]] = 1;
@@ -559,5 +566,60 @@ int rso_cauchy_decode(int w, int k, int m, const int *er, int e, uint8_t *blocks
             if (er[x] >= k) bitmatrix_apply(f, w, k, dat, C + (size_t)(er[x] - k) * k, blocks, B, P, er[x]);
     }
     free(C); free(Gs); free(Gi); free(surv); free(dat);
+    return rc;
+}
+
+int rso_cauchy_decode(int w, int k, int m, const int *er, int e, uint8_t *blocks, size_t B, size_t P) {
+    field_t *f;
+    if (cauchy_check(w, k, m, B, P, &f)) return -1;
+    if (check_erasures(k + m, m, er, e)) return -1;
+    uint32_t *C = (uint32_t *)malloc(sizeof(uint32_t) * (size_t)m * k);
+    if (!C) return -3;
+    rso_cauchy_matrix(w, k, m, C);
+    int rc = bitmatrix_code_decode(f, w, k, m, C, er, e, blocks, B, P);
+    free(C);
+    return rc;
+}
+
+/* ------------------------------------ polynomial code as a generator matrix */
+/* §6 (third direction): a generator polynomial can be turned into a
+ * generator matrix.  Column i of the m x k parity matrix holds the
+ * remainder of x^(m+i) divided by g(x): the parity of the unit data vector
+ * e_i, obtained here by the same long division as the encoder (Eq. 1). */
+int rso_polymat_matrix(int w, int k, int m, uint32_t *Pm) {
+    field_t *f;
+    if (check_code(w, k, m, &f)) return -1;
+    uint32_t d[256], p[256];
+    if (k > 256 || m > 256) return -1;
+    for (int i = 0; i < k; i++) {
+        for (int t = 0; t < k; t++) d[t] = (uint32_t)(t == i);
+        rso_poly_encode_column(w, k, m, d, p);
+        for (int j = 0; j < m; j++) Pm[(size_t)j * k + i] = p[j];
+    }
+    return 0;
+}
+
+/* §6 (first direction): the polynomial code's generator matrix in the
+ * bit-matrix (packet) layout of §2.3. */
+int rso_polybm_encode(int w, int k, int m, uint8_t *blocks, size_t B, size_t P) {
+    field_t *f;
+    if (cauchy_check(w, k, m, B, P, &f)) return -1;
+    uint32_t *C = (uint32_t *)malloc(sizeof(uint32_t) * (size_t)m * k);
+    if (!C) return -3;
+    rso_polymat_matrix(w, k, m, C);
+    int rc = bitmatrix_code_encode(f, w, k, m, C, blocks, B, P);
+    free(C);
+    return rc;
+}
+
+int rso_polybm_decode(int w, int k, int m, const int *er, int e, uint8_t *blocks, size_t B, size_t P) {
+    field_t *f;
+    if (cauchy_check(w, k, m, B, P, &f)) return -1;
+    if (check_erasures(k + m, m, er, e)) return -1;
+    uint32_t *C = (uint32_t *)malloc(sizeof(uint32_t) * (size_t)m * k);
+    if (!C) return -3;
+    rso_polymat_matrix(w, k, m, C);
+    int rc = bitmatrix_code_decode(f, w, k, m, C, er, e, blocks, B, P);
+    free(C);
     return rc;
 }
