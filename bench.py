@@ -113,6 +113,27 @@ def n_stripes():
     return DATA_BYTES // (K * BLOCK)
 
 
+def global_stripe(rank: int, s: int, per_rank: int) -> int:
+    """Stripe s of rank r is stripe r*per_rank + s of the world's data stream:
+    ranks shard the stripes with no overlap (weak scaling)."""
+    return rank * per_rank + s
+
+
+def max_over_ranks(value: float, world: int, device) -> float:
+    """Slowest rank's time (every rank gets it); no-op for one rank."""
+    if world <= 1:
+        return value
+    import torch
+    t = torch.tensor([value], dtype=torch.float64, device=device)
+    torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_rate(bytes_per_rank: int, world: int, seconds: float) -> float:
+    """Units processed by all ranks / the slowest rank's time."""
+    return world * bytes_per_rank / seconds
+
+
 def op_bytes(op: str) -> int:
     return (K + M) * BLOCK  # encode: read k, write m; decode (e = m, min-read): read k, write e
 
@@ -132,9 +153,9 @@ class Workload:
         self.bufs, self.batches, self.codes, self.ers, self.ops, self.shapes = {}, {}, {}, [], {}, {}
         data = torch.empty((self.S, K, BLOCK), dtype=torch.uint8, device=device)
         for s in range(self.S):
-            gs = rank * self.S + s
+            gs = global_stripe(rank, s, self.S)
             data[s] = inputs.random_bytes_torch(seed, gs * K * BLOCK, K * BLOCK, device).view(K, BLOCK)
-        self.ers = [inputs.erasure_pattern(seed, rank * self.S + s, self.n, M) for s in range(self.S)]
+        self.ers = [inputs.erasure_pattern(seed, global_stripe(rank, s, self.S), self.n, M) for s in range(self.S)]
         for real in REALIZATIONS:
             code = rs.Code(K, M, W, real, packet_bytes=PACKET if real == "cauchy" else None)
             # data and parity blocks of all stripes in two contiguous tensors
@@ -212,15 +233,12 @@ def run_ours(args, rank, world, device):
     clocks = sampler.stop() if sampler else None
     total_ms = t0.elapsed_time(t1)
     op_ms = {nm: sum(e[i].elapsed_time(e[i + 1]) for e in evs) / args.steps for i, nm in enumerate(names)}
-    if world > 1:
-        t = torch.tensor([total_ms], device=device)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        total_ms = float(t.item())
+    total_ms = max_over_ranks(total_ms, world, device)
     status = {real: (b[0].poll_status(), b[1].poll_status()) for real, b in wl.batches.items()}
 
     S = wl.S
     step_bytes = sum(S * op_bytes(op) for _, op in names)
-    value = world * args.steps * step_bytes / (total_ms * 1e-3) / 1e9
+    value = whole_job_rate(args.steps * step_bytes, world, total_ms * 1e-3) / 1e9
     user = world * args.steps * len(names) * S * K * BLOCK / (total_ms * 1e-3) / 1e9
     peak, kind = peaks()
     ops = {}

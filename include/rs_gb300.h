@@ -22,7 +22,8 @@
  *     failed kernel launch returns RS_ECUDA.  Kernel-side timeouts of the
  *     bounded shared-memory pipeline waits are reported through the code's
  *     device status word (rs_poll_status).  No C++ exception crosses the ABI.
- *   - Limits of the device path: n <= 64, m <= 8, n <= 2^w - 1.
+ *   - Limits of the device path: n <= 64, m <= 8 (m <= 4 for w = 16),
+ *     n <= 2^w - 1.
  */
 #ifndef RS_GB300_H
 #define RS_GB300_H
@@ -38,9 +39,13 @@ typedef struct rs_code rs_code;
 typedef struct rs_batch rs_batch;
 
 typedef enum {
-  RS_POLY = 0,         /* generator polynomial g(x) = prod_{i<m}(x + alpha^i), §3 */
-  RS_VANDERMONDE = 1,  /* systematic Vandermonde generator matrix, §2.2 */
-  RS_CAUCHY = 2        /* Cauchy generator, bit-matrix XOR over packets, §2.3 */
+  RS_POLY = 0,           /* generator polynomial g(x) = prod_{i<m}(x + alpha^i), §3 */
+  RS_VANDERMONDE = 1,    /* systematic Vandermonde generator matrix, §2.2 */
+  RS_CAUCHY = 2,         /* Cauchy generator, bit-matrix XOR over packets, §2.3 */
+  RS_POLY_MATRIX = 3,    /* the polynomial code through its generator matrix
+                            (column i = x^(m+i) mod g(x), §6); same bytes as RS_POLY */
+  RS_POLY_BITMATRIX = 4  /* that matrix's bit-matrix projection over packets
+                            (§6 with §2.3's packet layout) */
 } rs_realization;
 
 typedef enum {
@@ -66,7 +71,8 @@ int rs_version(void);
 const char *rs_last_error(void);
 
 /* Create a code.  §3.1 (g(x)), §2.2 (Vandermonde), §2.3 (Cauchy).
- *   k >= 1, m in [1, 8], k + m <= 64 and <= 2^w - 1, w in {8, 16},
+ *   k >= 1, m in [1, 8] (m in [1, 4] for w = 16), k + m <= 64 and
+ *   <= 2^w - 1, w in {8, 16},
  *   realization in rs_realization.
  * Builds the generator on the host and allocates a 4-byte device status
  * word on the current device.  *out receives the code (owned by the caller,
@@ -78,7 +84,8 @@ rs_status rs_init(int k, int m, int w, int realization, rs_code **out);
  * the code must have completed. */
 void rs_destroy(rs_code *code);
 
-/* Cauchy only: packet size P in bytes (§2.3 projection; default 2048).
+/* RS_CAUCHY and RS_POLY_BITMATRIX only: packet size P in bytes (§2.3
+ * projection; default 2048).
  * A block is a sequence of super-packets of w*P bytes; packet c of a
  * super-packet holds bit c of its 8P symbols.  P must be a positive
  * multiple of 128 (at most 1 MiB); block_bytes must then be a multiple of
@@ -98,7 +105,7 @@ rs_status rs_set_launch(rs_code *code, int consumer_warps, int depth, int ctas_p
  *   data_ptrs: host array of k device pointers (read only);
  *   parity_ptrs: host array of m device pointers (written);
  *   block_bytes: bytes per block (any value >= 0; even for w = 16; a multiple
- *   of w*P for RS_CAUCHY).  block_bytes = 0 is a no-op.
+ *   of w*P for the packet realizations).  block_bytes = 0 is a no-op.
  * Errors: RS_EINVAL (null code/pointer, misalignment, size), RS_ECUDA. */
 rs_status rs_encode(rs_code *code, const void *const *data_ptrs, void *const *parity_ptrs,
                     size_t block_bytes, void *stream);

@@ -35,29 +35,36 @@ NVCC_FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC,-O2",
 # 2 matrix encode, 3 matrix decode.  Layout: 0 symbol, 1 packet.
 # Kinds: 1 Vandermonde, 2 Cauchy.
 FIXED_CODES = [(8, 6, 3), (8, 10, 4), (8, 12, 4), (8, 20, 4), (16, 12, 4)]
+# compile-time generator-matrix forms of the polynomial code
+FIXED_POLY_MATRIX_CODES = [(8, 10, 4)]
 MIXED_POLY = [(8, (3, 4))]
+
+
+# m handled by the device path per w (GF(2^16): m <= 4)
+M_RANGE = {8: range(1, 9), 16: range(1, 5)}
 
 
 def instances():
     out = []
     for w in (8, 16):
-        for m in range(1, 9):
+        for m in M_RANGE[w]:
             for op in (0, 1):
                 out.append((f"poly_w{w}_m{m}_op{op}", f"PolyBody<{w}, {m}, {op}>",
                             dict(family=0, w=w, m=m, op=op)))
     for w in (8, 16):
-        for m in range(1, 9):
+        for m in M_RANGE[w]:
             for op in (2, 3):
                 for layout in (0, 1):
                     out.append((f"matrt_w{w}_m{m}_op{op}_l{layout}", f"MatRuntimeBody<{w}, {m}, {op}, {layout}>",
                                 dict(family=1, w=w, m=m, op=op, layout=layout)))
-    for (w, k, m) in FIXED_CODES:
-        for kind in (1, 2):
-            for op in (2, 3):
-                layout = 1 if kind == 2 else 0
-                out.append((f"matfix_w{w}_k{k}_m{m}_kind{kind}_op{op}",
-                            f"MatFixedBody<{w}, {k}, {m}, {kind}, {op}>",
-                            dict(family=2, w=w, m=m, op=op, layout=layout, kind=kind, k=k)))
+    fixed = [(c, kind) for c in FIXED_CODES for kind in (1, 2)] + \
+        [(c, kind) for c in FIXED_POLY_MATRIX_CODES for kind in (3, 4)]
+    for (w, k, m), kind in fixed:
+        for op in (2, 3):
+            layout = 1 if kind in (2, 4) else 0
+            out.append((f"matfix_w{w}_k{k}_m{m}_kind{kind}_op{op}",
+                        f"MatFixedBody<{w}, {k}, {m}, {kind}, {op}>",
+                        dict(family=2, w=w, m=m, op=op, layout=layout, kind=kind, k=k)))
     for (w, ms) in MIXED_POLY:
         bodies = ", ".join(f"PolyBody<{w}, {m}, {op}>" for m in ms for op in (0, 1))
         mset = sum(1 << m for m in ms)
@@ -142,7 +149,8 @@ def _stale(src: str, obj: str, hdr_mtime: float) -> bool:
 
 
 def _compile(src: str, obj: str, verbose: bool) -> tuple[str, str]:
-    cmd = [nvcc()] + ARCH + NVCC_FLAGS + ["-c", src, "-o", obj + ".tmp"]
+    extra = os.environ.get("RSGB_NVCC_EXTRA", "").split()
+    cmd = [nvcc()] + ARCH + NVCC_FLAGS + extra + ["-c", src, "-o", obj + ".tmp"]
     if verbose:
         cmd.insert(1, "-Xptxas=-v")
     if src.endswith(".cpp"):

@@ -23,6 +23,27 @@
 
 namespace rsgb {
 
+// Compile-time loop: f(Int<I>{}) for I = I0 .. N-1.
+template <int V>
+struct Int {
+  static constexpr int value = V;
+};
+
+template <int I, int N>
+struct StaticFor {
+  template <class F>
+  static RS_HD void run(F&& f) {
+    f(Int<I>{});
+    StaticFor<I + 1, N>::run(f);
+  }
+};
+template <int N>
+struct StaticFor<N, N> {
+  template <class F>
+  static RS_HD void run(F&&) {}
+};
+
+
 // Shifts by a constant, written as multiplies so that on the GPU they run
 // on the FMA pipe (IMAD / IMAD.HI) and leave the integer-logic pipe, which
 // bounds these kernels, to the XORs.
@@ -79,7 +100,8 @@ RS_HD void transpose<16>(uint32_t* x) {
   swap_round<16, 1, 1, 0x55555555u>(x);
 }
 
-// acc ^= E * in   (E a compile-time field element)
+// acc ^= E * in   (E a compile-time field element); the compiler folds
+// each row's XOR chain into 3-input logic instructions.
 template <int W, uint32_t E>
 RS_HD void mul_acc(uint32_t* acc, const uint32_t* in) {
   constexpr typename BitMatrix<W, E>::Rows M = BitMatrix<W, E>::value;

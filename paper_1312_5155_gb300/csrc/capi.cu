@@ -38,16 +38,18 @@ rs_status cuda_fail(cudaError_t e, const char* what) {
 }
 
 constexpr int kMaxGroups = 8;                        // kernels per batch launch
-constexpr int kKindOf[3] = {0, kKindVandermonde, kKindCauchy};
+constexpr int kKindOf[5] = {0, kKindVandermonde, kKindCauchy, kKindPolyMatrix, kKindPolyBitMatrix};
 
-bool has_fixed_kernels(int w, int k, int m) {
+bool packet_layout(Realization r) { return r == Realization::Cauchy || r == Realization::PolyBitMatrix; }
+
+bool has_fixed_kernels(int w, int k, int m, int kind) {
   KernelKey key;
   key.family = kFamMatFixed;
   key.w = w;
   key.m = m;
   key.op = kOpMatEncode;
-  key.layout = 0;
-  key.kind = kKindVandermonde;
+  key.layout = kind_layout(kind);
+  key.kind = kind;
   key.k = k;
   return find_kernel(key) != nullptr;
 }
@@ -109,8 +111,8 @@ rs_status check_blocks(const rs_code* c, const std::vector<const void*>& ptrs, s
     if (!aligned16(ptrs[i])) return fail(RS_EINVAL, "block pointers must be 16-byte aligned");
   }
   if (c->w == 16 && (bytes & 1u)) return fail(RS_EINVAL, "block_bytes must be even for w = 16");
-  if (c->real == Realization::Cauchy && bytes % ((size_t)c->w * c->packet_bytes))
-    return fail(RS_EINVAL, "block_bytes must be a multiple of w * packet_bytes for the Cauchy realization");
+  if (packet_layout(c->real) && bytes % ((size_t)c->w * c->packet_bytes))
+    return fail(RS_EINVAL, "block_bytes must be a multiple of w * packet_bytes for the bit-matrix realizations");
   if (bytes > ((size_t)1 << 40)) return fail(RS_EINVAL, "block_bytes too large");
   if (!disjoint(ptrs, bytes)) return fail(RS_EINVAL, "blocks of one operation must not overlap");
   return RS_OK;
@@ -158,7 +160,7 @@ rs_status select_kernel(const rs_code* c, int op, int M, PreparedOp& po) {
     key.op = op;  // kOpEncode / kOpDecode
   } else {
     key.op = op == kOpEncode ? kOpMatEncode : kOpMatDecode;
-    key.layout = c->real == Realization::Cauchy ? kLayoutPacket : kLayoutSymbol;
+    key.layout = packet_layout(c->real) ? kLayoutPacket : kLayoutSymbol;
     if (c->fixed) {
       key.family = kFamMatFixed;
       key.kind = kKindOf[(int)c->real];
@@ -176,8 +178,8 @@ rs_status select_kernel(const rs_code* c, int op, int M, PreparedOp& po) {
 void fill_common(const rs_code* c, size_t B, StripeDesc& d) {
   d.bytes = B;
   d.k = (uint8_t)c->k;
-  d.layout = c->real == Realization::Cauchy ? kLayoutPacket : kLayoutSymbol;
-  d.packet_bytes = c->real == Realization::Cauchy ? (uint32_t)c->packet_bytes : 0u;
+  d.layout = packet_layout(c->real) ? kLayoutPacket : kLayoutSymbol;
+  d.packet_bytes = packet_layout(c->real) ? (uint32_t)c->packet_bytes : 0u;
   d.pmask = (uint64_t)(uintptr_t)c->d_pmask;
 }
 
@@ -371,10 +373,10 @@ rs_status rs_init(int k, int m, int w, int realization, rs_code** out) {
   *out = nullptr;
   if (w != 8 && w != 16) return fail(RS_EINVAL, "w must be 8 or 16");
   if (k < 1 || m < 1) return fail(RS_EINVAL, "need k >= 1 and m >= 1");
-  if (realization < RS_POLY || realization > RS_CAUCHY) return fail(RS_EINVAL, "unknown realization");
+  if (realization < RS_POLY || realization > RS_POLY_BITMATRIX) return fail(RS_EINVAL, "unknown realization");
   if ((long)k + m > (1L << w) - 1) return fail(RS_EINVAL, "k + m must be <= 2^w - 1");
-  if (m > kMaxM || k + m > kMaxBlocks)
-    return fail(RS_EUNSUPPORTED, "device path limits: m <= 8 and k + m <= 64");
+  if (m > kMaxM || k + m > kMaxBlocks || (w == 16 && m > 4))
+    return fail(RS_EUNSUPPORTED, "device path limits: m <= 8 (m <= 4 for w = 16) and k + m <= 64");
   rs_code* c = new (std::nothrow) rs_code();
   if (!c) return fail(RS_ENOMEM, "host allocation failed");
   c->k = k;
@@ -388,8 +390,10 @@ rs_status rs_init(int k, int m, int w, int realization, rs_code** out) {
     }
   } else if (c->real == Realization::Cauchy) {
     cauchy_parity_matrix(k, m, w, c->P);
+  } else if (c->real != Realization::Poly) {
+    poly_parity_matrix(k, m, w, c->P);
   }
-  c->fixed = c->real != Realization::Poly && has_fixed_kernels(w, k, m);
+  c->fixed = c->real != Realization::Poly && has_fixed_kernels(w, k, m, kKindOf[(int)c->real]);
   cudaError_t e = cudaGetDevice(&c->device);
   if (e == cudaSuccess) e = cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, c->device);
   if (e == cudaSuccess) e = cudaMalloc(&c->d_status, sizeof(int));
@@ -420,7 +424,7 @@ void rs_destroy(rs_code* c) {
 
 rs_status rs_set_packet_bytes(rs_code* c, size_t packet_bytes) {
   if (!c) return fail(RS_EINVAL, "code is null");
-  if (c->real != Realization::Cauchy) return fail(RS_EINVAL, "packet size applies to the Cauchy realization only");
+  if (!packet_layout(c->real)) return fail(RS_EINVAL, "packet size applies to the bit-matrix realizations only");
   if (packet_bytes == 0 || packet_bytes % 128 || packet_bytes > (1u << 20))
     return fail(RS_EINVAL, "packet_bytes must be a positive multiple of 128 (at most 1 MiB)");
   c->packet_bytes = packet_bytes;

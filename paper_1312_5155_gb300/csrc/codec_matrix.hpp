@@ -26,25 +26,6 @@
 
 namespace rsgb {
 
-template <int V>
-struct Int {
-  static constexpr int value = V;
-};
-
-template <int I, int N>
-struct StaticFor {
-  template <class F>
-  static RS_HD void run(F&& f) {
-    f(Int<I>{});
-    StaticFor<I + 1, N>::run(f);
-  }
-};
-template <int N>
-struct StaticFor<N, N> {
-  template <class F>
-  static RS_HD void run(F&&) {}
-};
-
 // ------------------------------------------------ compile-time generators
 
 template <int K, int M>
@@ -86,11 +67,23 @@ RS_CHD constexpr bool ct_invert(uint32_t (&A)[K][K], uint32_t (&R)[K][K], int w)
 // Parity rows of the systematic generator.
 //   Vandermonde (§2.2): G = V_full V_top^-1 with V_full[r][c] = r^c.
 //   Cauchy (§2.3): C[i][j] = 1 / (i + (m + j)), X = {0..m-1}, Y = {m..m+k-1}.
+//   Polynomial code as a matrix (§6): column i = x^(m+i) mod g(x), since
+//   x^m d(x) mod g = sum_i d_i (x^(m+i) mod g) (Eq. 1).
 template <int W, int K, int M, int KIND>
 struct ParityMatrix {
   static constexpr MatKM<K, M> make() {
     MatKM<K, M> P{};
-    if (KIND == kKindCauchy) {
+    if (KIND == kKindPolyMatrix || KIND == kKindPolyBitMatrix) {
+      const GenPoly g = make_genpoly(W, M);
+      uint32_t r[M] = {};
+      for (int j = 0; j < M; ++j) r[j] = g.c[j];  // x^m = sum_{j<m} g_j x^j (mod g, char 2)
+      for (int i = 0; i < K; ++i) {
+        for (int j = 0; j < M; ++j) P.a[j][i] = r[j];
+        const uint32_t top = r[M - 1];  // multiply by x and reduce
+        for (int j = M - 1; j >= 1; --j) r[j] = r[j - 1] ^ gf_mul(top, g.c[j], W);
+        r[0] = gf_mul(top, g.c[0], W);
+      }
+    } else if (KIND == kKindCauchy) {
       for (int i = 0; i < M; ++i)
         for (int j = 0; j < K; ++j) P.a[i][j] = gf_inv((uint32_t)i ^ (uint32_t)(M + j), W);
     } else {
@@ -184,15 +177,7 @@ struct MatDecodeFixed {
         for (int b = 0; b < W; ++b) S[j][b] ^= x[b];
       }
     }
-    uint32_t out[M][W];
-    apply_runtime_matrix<W, M>(out, S, e, wm);
-#pragma unroll
-    for (int t = 0; t < M; ++t) {
-      if (t < e) {
-        if (kTranspose) transpose<W>(out[t]);
-        dst.store(t, out[t]);
-      }
-    }
+    ApplyDispatch<W, M, kTranspose>::run(e, S, wm, dst);
   }
 };
 
@@ -256,15 +241,7 @@ struct MatDecodeRuntime {
         for (int b = 0; b < W; ++b) S[j][b] ^= x[b];
       }
     }
-    uint32_t out[M][W];
-    apply_runtime_matrix<W, M>(out, S, e, wm);
-#pragma unroll
-    for (int t = 0; t < M; ++t) {
-      if (t < e) {
-        if (kTranspose) transpose<W>(out[t]);
-        dst.store(t, out[t]);
-      }
-    }
+    ApplyDispatch<W, M, kTranspose>::run(e, S, wm, dst);
   }
 };
 

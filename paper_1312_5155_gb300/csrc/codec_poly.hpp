@@ -17,24 +17,62 @@ namespace rsgb {
 // After the k data symbols, r_j is the coefficient of x^j of the remainder,
 // i.e. parity p_j.  All g_j are compile-time constants (they depend on m
 // only), so every product is a fixed XOR pattern over bit-planes.
-template <int W, int M, int J>
-struct LfsrShift {
-  static RS_HD void run(uint32_t (*r)[W], const uint32_t* f) {
-#pragma unroll
-    for (int b = 0; b < W; ++b) r[J][b] = r[J - 1][b];
-    mul_acc<W, GenPolyOf<W, M>::value.c[J]>(r[J], f);
-    LfsrShift<W, M, J - 1>::run(r, f);
-  }
-};
-template <int W, int M>
-struct LfsrShift<W, M, 0> {
-  static RS_HD void run(uint32_t (*r)[W], const uint32_t* f) {
-    mul_set<W, GenPolyOf<W, M>::value.c[0]>(r[0], f);
-  }
-};
-
+// One LFSR step with register renaming: after S steps (mod M) logical r_j
+// lives in physical register (j - S) mod M.  Then every update is in place:
+// new r_j = old r_{j-1} + g_j f lands in the register that held r_{j-1}, and
+// new r_0 = g_0 f in the one that held r_{m-1} (already folded into f).  M
+// consecutive steps return the mapping to the identity, so a runtime loop
+// over groups of M steps needs no register moves.
 template <int W, int M>
 struct PolyEncode {
+  static constexpr int phys(int j, int S) { return ((j - S) % M + M) % M; }
+
+  template <int S>
+  static RS_HD void step(uint32_t (*r)[W], const uint32_t* x) {
+    constexpr int top = phys(M - 1, S);
+    uint32_t f[W];
+#pragma unroll
+    for (int b = 0; b < W; ++b) f[b] = x[b] ^ r[top][b];
+    StaticFor<1, M>::run([&](auto J) {
+      constexpr int j = decltype(J)::value;
+      mul_acc<W, GenPolyOf<W, M>::value.c[j]>(r[phys(j - 1, S)], f);
+    });
+    mul_set<W, GenPolyOf<W, M>::value.c[0]>(r[top], f);
+  }
+
+  template <int S, class Src>
+  static RS_HD void load_step(int i, uint32_t (*r)[W], Src& src) {
+    uint32_t x[W];
+    src.load(i, x);
+    transpose<W>(x);
+    step<S>(r, x);
+  }
+
+  // Remaining R < M steps after the grouped loop, then the stores with the
+  // mapping rotated by R.
+  template <int R, class Src, class Dst>
+  static RS_HD void finish(int i, int rem, uint32_t (*r)[W], Src& src, Dst& dst) {
+    if constexpr (R < M) {
+      if (rem == R) {
+        StaticFor<0, R>::run([&](auto S) { load_step<decltype(S)::value>(i + decltype(S)::value, r, src); });
+        StaticFor<0, M>::run([&](auto J) {
+          constexpr int p = phys(decltype(J)::value, R);
+          transpose<W>(r[p]);
+          dst.store(decltype(J)::value, r[p]);
+        });
+        return;
+      }
+      finish<R + 1>(i, rem, r, src, dst);
+    }
+  }
+
+  // §3.2 Eq. 1: p(x) = x^m d(x) mod g(x).  Division by the monic g(x) as a
+  // linear-feedback shift register fed with the data symbols from the highest
+  // degree down (d_{k-1} first, since d_i sits at x^(m+i)):
+  //   f = d_i + r_{m-1};  r_j = r_{j-1} + g_j f (j = m-1..1);  r_0 = g_0 f.
+  // After the k data symbols, r_j is the coefficient of x^j of the remainder,
+  // i.e. parity p_j.  All g_j are compile-time constants (they depend on m
+  // only), so every product is a fixed XOR pattern over bit-planes.
   // inputs: k data blocks in the order d_{k-1}, ..., d_0; outputs p_0..p_{m-1}
   template <class Src, class Dst>
   static RS_HD void run(int k, Src& src, Dst& dst) {
@@ -43,20 +81,11 @@ struct PolyEncode {
     for (int j = 0; j < M; ++j)
 #pragma unroll
       for (int b = 0; b < W; ++b) r[j][b] = 0;
-    for (int i = 0; i < k; ++i) {
-      uint32_t x[W];
-      src.load(i, x);
-      transpose<W>(x);
-      uint32_t f[W];
-#pragma unroll
-      for (int b = 0; b < W; ++b) f[b] = x[b] ^ r[M - 1][b];
-      LfsrShift<W, M, M - 1>::run(r, f);
+    int i = 0;
+    for (; i + M <= k; i += M) {
+      StaticFor<0, M>::run([&](auto S) { load_step<decltype(S)::value>(i + decltype(S)::value, r, src); });
     }
-#pragma unroll
-    for (int j = 0; j < M; ++j) {
-      transpose<W>(r[j]);
-      dst.store(j, r[j]);
-    }
+    finish<0>(i, k - i, r, src, dst);
   }
 };
 
@@ -69,29 +98,55 @@ struct PolyEncode {
 // the host inverts the M x M Vandermonde system once per erasure pattern;
 // output t is sum_j W[t][j] S_j with the runtime matrix W (rows of the
 // inverse for the erased blocks).
-template <int W, int M, int J>
-struct HornerMul {
-  static RS_HD void run(uint32_t (*S)[W]) {
-    uint32_t t[W];
+// Multiply by alpha in place under register renaming: logical plane b of
+// the value lives in physical register (b - ROT) mod W.  The shift of the
+// planes is the renaming itself (ROT grows by one); only the fold of the top
+// plane through the primitive polynomial costs XORs.
+template <int W, int ROT>
+RS_HD void mul_alpha_renamed(uint32_t* x) {
+  constexpr uint32_t low = prim_poly(W) & ((1u << W) - 1u);
+  constexpr int np = ROT + 1;                       // rotation after the step
+  constexpr int top = ((0 - np) % W + W) % W;       // new logical 0 = old logical W-1
 #pragma unroll
-    for (int b = 0; b < W; ++b) t[b] = S[J][b];
-    mul_set<W, gf_alpha_pow(J, W)>(S[J], t);
-    HornerMul<W, M, J - 1>::run(S);
+  for (int r = 1; r < W; ++r) {
+    if ((low >> r) & 1u) x[((r - np) % W + W) % W] ^= x[top];
   }
-};
-template <int W, int M>
-struct HornerMul<W, M, 0> {
-  static RS_HD void run(uint32_t (*)[W]) {}  // alpha^0 = 1
-};
+}
 
-// out[t] = sum_j W[t][j] S_j for t < e, with W as packed bits (entry (t, j)).
-// For every syndrome j the chain alpha^c S_j (c = 0..W-1) is walked once and
-// shared by all outputs; each chain term costs one AND-XOR per plane.  S is
-// clobbered.
-template <int W, int M>
-RS_HD void apply_runtime_matrix(uint32_t (*out)[W], uint32_t (*S)[W], int e, const PackedBits<W, M, M>& wm) {
+// Syndrome j multiplied by alpha^j at step s of a group: j renamed alpha
+// steps, starting from rotation j*s.
+template <int W, int M, int s>
+RS_HD void horner_mul(uint32_t (*S)[W]) {
+  StaticFor<1, M>::run([&](auto J) {
+    constexpr int j = decltype(J)::value;
+    StaticFor<0, j>::run([&](auto T) {
+      mul_alpha_renamed<W, (j * s + decltype(T)::value) % W>(S[j]);
+    });
+  });
+}
+
+// Add input x (planes) into every syndrome at rotation state after step s.
+template <int W, int M, int s>
+RS_HD void horner_add(uint32_t (*S)[W], const uint32_t* x) {
 #pragma unroll
-  for (int t = 0; t < M; ++t)
+  for (int b = 0; b < W; ++b) S[0][b] ^= x[b];
+  StaticFor<1, M>::run([&](auto J) {
+    constexpr int j = decltype(J)::value;
+    constexpr int rot = (j * (s + 1)) % W;
+#pragma unroll
+    for (int b = 0; b < W; ++b) S[j][((b - rot) % W + W) % W] ^= x[b];
+  });
+}
+
+// out[t] = sum_j W[t][j] S_j for t < E, with W as packed bits (entry (t, j)).
+// For every syndrome j the chain alpha^c S_j (c = 0..W-1) is walked once and
+// shared by all outputs; each chain term costs one AND-XOR per plane.  E is a
+// compile-time count (the caller dispatches on the runtime e once), so no
+// per-term guards are emitted.  S is clobbered.
+template <int W, int M, int E>
+RS_HD void apply_runtime_matrix_e(uint32_t (*out)[W], uint32_t (*S)[W], const PackedBits<W, M, M>& wm) {
+#pragma unroll
+  for (int t = 0; t < E; ++t)
 #pragma unroll
     for (int b = 0; b < W; ++b) out[t][b] = 0;
 #pragma unroll
@@ -99,17 +154,45 @@ RS_HD void apply_runtime_matrix(uint32_t (*out)[W], uint32_t (*S)[W], int e, con
 #pragma unroll
     for (int c = 0; c < W; ++c) {
 #pragma unroll
-      for (int t = 0; t < M; ++t) {
-        if (t < e) {
-          const uint32_t mk = wm.mask(t, j, c);
+      for (int t = 0; t < E; ++t) {
+        const uint32_t mk = wm.mask(t, j, c);
 #pragma unroll
-          for (int b = 0; b < W; ++b) out[t][b] ^= S[j][b] & mk;
-        }
+        for (int b = 0; b < W; ++b) out[t][b] ^= S[j][b] & mk;
       }
       if (c + 1 < W) mul_alpha<W>(S[j]);
     }
   }
 }
+
+// Apply the runtime matrix for the e outputs and store them (symbols ->
+// planes back with kTranspose).
+template <int W, int M, int E, bool kTranspose, class Dst>
+RS_HD void apply_and_store(uint32_t (*S)[W], const PackedBits<W, M, M>& wm, Dst& dst) {
+  uint32_t out[E][W];
+  apply_runtime_matrix_e<W, M, E>(out, S, wm);
+#pragma unroll
+  for (int t = 0; t < E; ++t) {
+    if (kTranspose) transpose<W>(out[t]);
+    dst.store(t, out[t]);
+  }
+}
+
+template <int W, int M, bool kTranspose, int E = M>
+struct ApplyDispatch {
+  template <class Dst>
+  static RS_HD void run(int e, uint32_t (*S)[W], const PackedBits<W, M, M>& wm, Dst& dst) {
+    if (e == E) {
+      apply_and_store<W, M, E, kTranspose>(S, wm, dst);
+      return;
+    }
+    ApplyDispatch<W, M, kTranspose, E - 1>::run(e, S, wm, dst);
+  }
+};
+template <int W, int M, bool kTranspose>
+struct ApplyDispatch<W, M, kTranspose, 0> {
+  template <class Dst>
+  static RS_HD void run(int, uint32_t (*)[W], const PackedBits<W, M, M>&, Dst&) {}
+};
 
 template <int W, int M>
 struct PolyDecode {
@@ -124,28 +207,27 @@ struct PolyDecode {
     for (int j = 0; j < M; ++j)
 #pragma unroll
       for (int b = 0; b < W; ++b) S[j][b] = 0;
+    // Horner over positions in groups of W steps (the renaming period);
+    // the count is padded at the top with positions that hold no data,
+    // which leave the zero start value unchanged.
+    const int groups = (n_pos + W - 1) / W;
+    int pos = groups * W - 1;
     int i = 0;
-    for (int pos = n_pos - 1; pos >= 0; --pos) {
-      HornerMul<W, M, M - 1>::run(S);
-      if ((read_mask >> pos) & 1ull) {
-        uint32_t x[W];
-        src.load(i++, x);
-        transpose<W>(x);
-#pragma unroll
-        for (int j = 0; j < M; ++j)
-#pragma unroll
-          for (int b = 0; b < W; ++b) S[j][b] ^= x[b];
-      }
+    for (int g = 0; g < groups; ++g) {
+      StaticFor<0, W>::run([&](auto St) {
+        constexpr int st = decltype(St)::value;
+        const int p = pos - st;
+        horner_mul<W, M, st>(S);
+        if (p < n_pos && ((read_mask >> p) & 1ull)) {
+          uint32_t x[W];
+          src.load(i++, x);
+          transpose<W>(x);
+          horner_add<W, M, st>(S, x);
+        }
+      });
+      pos -= W;
     }
-    uint32_t out[M][W];
-    apply_runtime_matrix<W, M>(out, S, e, wm);
-#pragma unroll
-    for (int t = 0; t < M; ++t) {
-      if (t < e) {
-        transpose<W>(out[t]);
-        dst.store(t, out[t]);
-      }
-    }
+    ApplyDispatch<W, M, true>::run(e, S, wm, dst);
   }
 };
 

@@ -23,7 +23,12 @@ enum : uint8_t {
 enum : uint8_t { kLayoutSymbol = 0, kLayoutPacket = 1 };
 
 // Matrix realizations with a compile-time generator
-enum : int { kKindVandermonde = 1, kKindCauchy = 2 };
+enum : int { kKindVandermonde = 1, kKindCauchy = 2, kKindPolyMatrix = 3, kKindPolyBitMatrix = 4 };
+
+// Layout of a matrix kind: the bit-matrix kinds keep §2.3's packet layout.
+RS_CHD constexpr int kind_layout(int kind) {
+  return (kind == kKindCauchy || kind == kKindPolyBitMatrix) ? 1 : 0;
+}
 
 struct StripeDesc {
   uint64_t bytes;       // block bytes B
@@ -72,6 +77,26 @@ struct JobParams {
   uint64_t inl_ptrs[kMaxPtrs];
   uint32_t inl_coef[kMaxCoefWords];
 };
+
+// What the producer tells the consumers about a tile, written into shared
+// memory next to the tile's first slot before that slot is armed (so the
+// slot's full barrier publishes it).  Consumers copy what they need into
+// registers before they release that slot.
+constexpr int kHeaderCoefWords = (kMaxM * kMaxM * 16 + 31) / 32;
+struct alignas(16) TileHeader {
+  uint64_t goff;
+  uint64_t read_mask;
+  uint64_t pmask;
+  uint64_t ptrs;            // this stripe's pointer table (ragged-end reads)
+  uint64_t outp[kMaxM];
+  uint32_t len;
+  uint32_t span_off;
+  uint32_t packet_bytes;
+  uint16_t n_in, n_out;
+  uint8_t op, m, k, n_pos, e, pad[3];
+  uint32_t coef[kHeaderCoefWords];
+};
+constexpr uint32_t kHeaderBytes = (uint32_t)((sizeof(TileHeader) + 127) / 128 * 128);
 
 // Bytes of one warp segment (32 lanes x 32 symbols) in the symbol layout.
 RS_CHD constexpr uint32_t segment_bytes(int w) { return 32u * 32u * (uint32_t)(w / 8); }

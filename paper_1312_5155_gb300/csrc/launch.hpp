@@ -29,8 +29,10 @@ struct TuneCfg {
 void set_last_error(const std::string& msg);
 void clear_last_error();
 
+// Dynamic shared memory of a launch: mbarriers, one tile header per slot,
+// the slots.
 inline size_t ring_smem_bytes(uint32_t depth, uint32_t slice) {
-  return ((2u * depth * 8u + 127u) & ~127u) + (size_t)depth * slice;
+  return ((2u * depth * 8u + 127u) & ~127u) + (size_t)depth * (kHeaderBytes + slice);
 }
 
 

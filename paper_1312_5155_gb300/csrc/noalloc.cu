@@ -66,7 +66,8 @@ extern "C" rs_status rs_poly_encode_stripes_noalloc(int k, int m, int w, int n_s
   if (w != 8 && w != 16) return fail_na(RS_EINVAL, "w must be 8 or 16");
   if (k < 1 || m < 1) return fail_na(RS_EINVAL, "need k >= 1 and m >= 1");
   if ((long)k + m > (1L << w) - 1) return fail_na(RS_EINVAL, "k + m must be <= 2^w - 1");
-  if (m > kMaxM || k + m > kMaxBlocks) return fail_na(RS_EUNSUPPORTED, "device path limits: m <= 8, k + m <= 64");
+  if (m > kMaxM || k + m > kMaxBlocks || (w == 16 && m > 4))
+    return fail_na(RS_EUNSUPPORTED, "device path limits: m <= 8 (m <= 4 for w = 16), k + m <= 64");
   if (n_stripes < 0) return fail_na(RS_EINVAL, "negative stripe count");
   if (n_stripes == 0) {
     rsgb::clear_last_error();

@@ -221,4 +221,17 @@ void cauchy_parity_matrix(int k, int m, int w, std::vector<uint32_t>& P) {
     for (int j = 0; j < k; ++j) P[(size_t)i * k + j] = gf_inv((uint32_t)i ^ (uint32_t)(m + j), w);
 }
 
+void poly_parity_matrix(int k, int m, int w, std::vector<uint32_t>& P) {
+  const GenPoly g = make_genpoly(w, m);
+  P.assign((size_t)m * k, 0);
+  std::vector<uint32_t> r(m);
+  for (int j = 0; j < m; ++j) r[j] = g.c[j];
+  for (int i = 0; i < k; ++i) {
+    for (int j = 0; j < m; ++j) P[(size_t)j * k + i] = r[j];
+    const uint32_t top = r[m - 1];
+    for (int j = m - 1; j >= 1; --j) r[j] = r[j - 1] ^ gf_mul(top, g.c[j], w);
+    r[0] = gf_mul(top, g.c[0], w);
+  }
+}
+
 }  // namespace rsgb

@@ -90,6 +90,13 @@ __device__ __forceinline__ TileGeom tile_geom(const StripeDesc& d, uint32_t lt, 
   return g;
 }
 
+// The per-tile operation fields a body needs, held in registers.
+struct TileOp {
+  uint64_t read_mask;
+  uint64_t pmask;
+  int k, n_pos, e, m, op;
+};
+
 __device__ __forceinline__ void wait_or_fail(uint64_t* bar, uint32_t par, bool& failed, int* status, int code,
                                              unsigned long long limit) {
   if (!failed && !mbar_wait(bar, par, limit)) {
@@ -99,10 +106,11 @@ __device__ __forceinline__ void wait_or_fail(uint64_t* bar, uint32_t par, bool& 
 }
 
 // ------------------------------------------------------ consumer tile views
-template <int W>
+template <int W, int MO>
 struct SymTile {
   Ring* ring;
   const uint64_t* ptrs;  // stripe pointers: inputs then outputs
+  uint64_t outp[MO];     // output pointers, loaded at tile start
   int n_in;
   uint64_t goff;   // byte offset of the tile within each block
   uint32_t len;    // valid bytes of this tile (<= slice)
@@ -112,25 +120,17 @@ struct SymTile {
   unsigned long long limit;
   bool failed;
 
-  __device__ __forceinline__ void begin(const StripeDesc& d, const TileGeom& g, const uint64_t* p) {
-    ptrs = p;
-    n_in = d.n_in;
-    goff = g.goff;
-    len = g.len;
-  }
-
-  // Inputs are consumed in order 0..n_in-1; load(i) hands out input i
-  // (fetched while step i-1 was computing) and starts fetching input i+1,
-  // so the slot wait and shared-memory latency overlap the arithmetic.
-  uint32_t nxt[W];
-  __device__ __forceinline__ void load(int i, uint32_t* x) {
-    if (i == 0) fetch(0, nxt);
+  __device__ __forceinline__ void begin(const TileHeader& h) {
+    ptrs = reinterpret_cast<const uint64_t*>(h.ptrs);
+    n_in = h.n_in;
+    goff = h.goff;
+    len = h.len;
 #pragma unroll
-    for (int b = 0; b < W; ++b) x[b] = nxt[b];
-    if (i + 1 < n_in) fetch(i + 1, nxt);
+    for (int t = 0; t < MO; ++t) outp[t] = h.outp[t];
   }
 
-  __device__ __forceinline__ void fetch(int i, uint32_t* x) {
+  // Inputs are consumed in order 0..n_in-1, one ring slot each.
+  __device__ __forceinline__ void load(int i, uint32_t* x) {
     Ring& r = *ring;
     const uint32_t s = r.s, par = r.par;
     r.advance();
@@ -166,7 +166,7 @@ struct SymTile {
 
   __device__ __forceinline__ void store(int t, const uint32_t* x) {
     if (failed) return;
-    uint8_t* out = reinterpret_cast<uint8_t*>(ptrs[n_in + t]) + goff;
+    uint8_t* out = reinterpret_cast<uint8_t*>(outp[t]) + goff;
 #pragma unroll
     for (int c = 0; c < W / 4; ++c) {
       const uint32_t co = seg + (uint32_t)c * 512u + lane * 16u;
@@ -181,10 +181,11 @@ struct SymTile {
   }
 };
 
-template <int W>
+template <int W, int MO>
 struct PacketTile {
   Ring* ring;
   const uint64_t* ptrs;
+  uint64_t outp[MO];  // output pointers, loaded at tile start
   int n_in;
   uint64_t goff;      // super-packet offset
   uint32_t span_off;  // offset inside each packet
@@ -195,23 +196,17 @@ struct PacketTile {
   unsigned long long limit;
   bool failed;
 
-  __device__ __forceinline__ void begin(const StripeDesc& d, const TileGeom& g, const uint64_t* p) {
-    ptrs = p;
-    n_in = d.n_in;
-    goff = g.goff;
-    span_off = g.span_off;
-    P = d.packet_bytes;
-  }
-
-  uint32_t nxt[W];
-  __device__ __forceinline__ void load(int i, uint32_t* x) {
-    if (i == 0) fetch(0, nxt);
+  __device__ __forceinline__ void begin(const TileHeader& h) {
+    ptrs = reinterpret_cast<const uint64_t*>(h.ptrs);
+    n_in = h.n_in;
+    goff = h.goff;
+    span_off = h.span_off;
+    P = h.packet_bytes;
 #pragma unroll
-    for (int b = 0; b < W; ++b) x[b] = nxt[b];
-    if (i + 1 < n_in) fetch(i + 1, nxt);
+    for (int t = 0; t < MO; ++t) outp[t] = h.outp[t];
   }
 
-  __device__ __forceinline__ void fetch(int i, uint32_t* x) {
+  __device__ __forceinline__ void load(int i, uint32_t* x) {
     Ring& r = *ring;
     const uint32_t s = r.s, par = r.par;
     r.advance();
@@ -225,7 +220,7 @@ struct PacketTile {
 
   __device__ __forceinline__ void store(int t, const uint32_t* x) {
     if (failed) return;
-    uint8_t* out = reinterpret_cast<uint8_t*>(ptrs[n_in + t]) + goff + span_off + 4u * word;
+    uint8_t* out = reinterpret_cast<uint8_t*>(outp[t]) + goff + span_off + 4u * word;
 #pragma unroll
     for (int c = 0; c < W; ++c) *reinterpret_cast<uint32_t*>(out + (size_t)c * P) = x[c];
   }
@@ -263,16 +258,17 @@ template <int W, int M, int OP>
 struct PolyBody {
   static constexpr int kW = W;
   static constexpr int kLayout = kLayoutSymbol;
+  static constexpr int kMaxOut = M;
   static constexpr int kMaxWarps = OP == kOpEncode ? body_warps(M * W) : 8;
   static constexpr int kMinBlocks = body_min_blocks(W, kMaxWarps, (OP == kOpEncode ? 1 : 2) * M * W);
-  __device__ static bool matches(const StripeDesc& d) { return d.op == OP && d.m == M; }
+  __device__ static bool matches(const TileOp& o) { return o.op == OP && o.m == M; }
   template <class Tile>
-  __device__ static void run(const StripeDesc& d, Tile& t, const uint32_t* coef) {
+  __device__ static void run(const TileOp& o, Tile& t, const uint32_t* coef) {
     if constexpr (OP == kOpEncode) {
-      PolyEncode<W, M>::run((int)d.k, t, t);
+      PolyEncode<W, M>::run(o.k, t, t);
     } else {
-      CoefWords cm{coef + d.coef_off};
-      PolyDecode<W, M>::run((int)d.n_pos, d.read_mask, (int)d.e, t, t, cm);
+      CoefWords cm{coef};
+      PolyDecode<W, M>::run(o.n_pos, o.read_mask, o.e, t, t, cm);
     }
   }
 };
@@ -281,17 +277,18 @@ template <int W, int M, int OP, int LAYOUT>
 struct MatRuntimeBody {
   static constexpr int kW = W;
   static constexpr int kLayout = LAYOUT;
+  static constexpr int kMaxOut = M;
   static constexpr int kMaxWarps = OP == kOpMatEncode ? body_warps(M * W + 16) : 8;
   static constexpr int kMinBlocks = body_min_blocks(W, kMaxWarps, (OP == kOpMatEncode ? 1 : 2) * M * W + 16);
-  __device__ static bool matches(const StripeDesc& d) { return d.op == OP && d.m == M; }
+  __device__ static bool matches(const TileOp& o) { return o.op == OP && o.m == M; }
   template <class Tile>
-  __device__ static void run(const StripeDesc& d, Tile& t, const uint32_t* coef) {
-    ColumnWords<W, M> cols{reinterpret_cast<const uint32_t*>(d.pmask)};
+  __device__ static void run(const TileOp& o, Tile& t, const uint32_t* coef) {
+    ColumnWords<W, M> cols{reinterpret_cast<const uint32_t*>(o.pmask)};
     if constexpr (OP == kOpMatEncode) {
-      MatEncodeRuntime<W, M, LAYOUT == kLayoutSymbol>::run((int)d.k, t, t, cols);
+      MatEncodeRuntime<W, M, LAYOUT == kLayoutSymbol>::run(o.k, t, t, cols);
     } else {
-      CoefWords cm{coef + d.coef_off};
-      MatDecodeRuntime<W, M, LAYOUT == kLayoutSymbol>::run((int)d.k, d.read_mask, (int)d.e, t, t, cols, cm);
+      CoefWords cm{coef};
+      MatDecodeRuntime<W, M, LAYOUT == kLayoutSymbol>::run(o.k, o.read_mask, o.e, t, t, cols, cm);
     }
   }
 };
@@ -299,17 +296,18 @@ struct MatRuntimeBody {
 template <int W, int K, int M, int KIND, int OP>
 struct MatFixedBody {
   static constexpr int kW = W;
-  static constexpr int kLayout = KIND == kKindCauchy ? kLayoutPacket : kLayoutSymbol;
+  static constexpr int kLayout = kind_layout(KIND);
+  static constexpr int kMaxOut = M;
   static constexpr int kMaxWarps = OP == kOpMatEncode ? body_warps(M * W) : 8;
   static constexpr int kMinBlocks = body_min_blocks(W, kMaxWarps, (OP == kOpMatEncode ? 1 : 2) * M * W);
-  __device__ static bool matches(const StripeDesc& d) { return d.op == OP && d.m == M && d.k == K; }
+  __device__ static bool matches(const TileOp& o) { return o.op == OP && o.m == M && o.k == K; }
   template <class Tile>
-  __device__ static void run(const StripeDesc& d, Tile& t, const uint32_t* coef) {
+  __device__ static void run(const TileOp& o, Tile& t, const uint32_t* coef) {
     if constexpr (OP == kOpMatEncode) {
       MatEncodeFixed<W, K, M, KIND, kLayout == kLayoutSymbol>::run(t, t);
     } else {
-      CoefWords cm{coef + d.coef_off};
-      MatDecodeFixed<W, K, M, KIND, kLayout == kLayoutSymbol>::run(d.read_mask, (int)d.e, t, t, cm);
+      CoefWords cm{coef};
+      MatDecodeFixed<W, K, M, KIND, kLayout == kLayoutSymbol>::run(o.read_mask, o.e, t, t, cm);
     }
   }
 };
@@ -326,27 +324,34 @@ struct MixedBody {
     return w;
   }
   static constexpr int kMaxWarps = min_warps();
+  static constexpr int max_out() {
+    int o = First::kMaxOut;
+    ((o = Rest::kMaxOut > o ? Rest::kMaxOut : o), ...);
+    return o;
+  }
+  static constexpr int kMaxOut = max_out();
   static constexpr int min_blocks() {
     int b = First::kMinBlocks;
     ((b = Rest::kMinBlocks < b ? Rest::kMinBlocks : b), ...);
     return b;
   }
   static constexpr int kMinBlocks = min_blocks();
-  __device__ static bool matches(const StripeDesc& d) { return First::matches(d) || (Rest::matches(d) || ...); }
+  __device__ static bool matches(const TileOp& o) { return First::matches(o) || (Rest::matches(o) || ...); }
   template <class Tile>
-  __device__ static void run(const StripeDesc& d, Tile& t, const uint32_t* coef) {
-    if (First::matches(d)) {
-      First::run(d, t, coef);
+  __device__ static void run(const TileOp& o, Tile& t, const uint32_t* coef) {
+    if (First::matches(o)) {
+      First::run(o, t, coef);
       return;
     }
-    if constexpr (sizeof...(Rest) > 0) MixedBody<Rest...>::run(d, t, coef);
+    if constexpr (sizeof...(Rest) > 0) MixedBody<Rest...>::run(o, t, coef);
   }
 };
 
 // ---------------------------------------------------------------- producer
 template <int W, int LAYOUT>
 __device__ __forceinline__ void producer_loop(const JobParams& p, const StripeDesc* stripes, const uint64_t* ptrs,
-                                              Ring& ring, uint32_t n_stripes, uint32_t total_tiles) {
+                                              const uint32_t* coef, TileHeader* headers, Ring& ring,
+                                              uint32_t n_stripes, uint32_t total_tiles) {
   if (p.inject == kInjectProducerStall && blockIdx.x == 0) return;  // test hook, see job.hpp
   uint32_t q = 0;
   bool ok = true;
@@ -360,6 +365,29 @@ __device__ __forceinline__ void producer_loop(const JobParams& p, const StripeDe
         record_status(p.status, kDevErrTimeoutEmpty);
         ok = false;
         break;
+      }
+      if (i == 0) {
+        // the tile's header travels with its first slot
+        TileHeader& h = headers[s];
+        h.goff = g.goff;
+        h.len = g.len;
+        h.span_off = g.span_off;
+        h.read_mask = d.read_mask;
+        h.pmask = d.pmask;
+        h.ptrs = reinterpret_cast<uint64_t>(ip);
+        h.packet_bytes = d.packet_bytes;
+        h.n_in = d.n_in;
+        h.n_out = d.n_out;
+        h.op = d.op;
+        h.m = d.m;
+        h.k = d.k;
+        h.n_pos = d.n_pos;
+        h.e = d.e;
+        for (int t = 0; t < kMaxM; ++t) h.outp[t] = t < (int)d.n_out ? ip[d.n_in + t] : 0ull;
+        if (d.op == kOpDecode || d.op == kOpMatDecode) {
+          const int words = ((int)d.m * (int)d.m * W + 31) / 32;
+          for (int q = 0; q < words; ++q) h.coef[q] = coef[d.coef_off + q];
+        }
       }
       uint8_t* dst = ring.slots + (size_t)s * ring.slice;
       const uint8_t* src = reinterpret_cast<const uint8_t*>(ip[i]) + g.goff;
@@ -400,7 +428,8 @@ __global__ void __launch_bounds__((Body::kMaxWarps + 1) * 32, Body::kMinBlocks)
   Ring ring;
   ring.full = reinterpret_cast<uint64_t*>(smem);
   ring.empty = ring.full + depth;
-  ring.slots = smem + ((2u * depth * 8u + 127u) & ~127u);
+  TileHeader* headers = reinterpret_cast<TileHeader*>(smem + ((2u * depth * 8u + 127u) & ~127u));
+  ring.slots = reinterpret_cast<uint8_t*>(headers) + (size_t)depth * kHeaderBytes;
   ring.depth = depth;
   ring.slice = p.slice_bytes;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -420,11 +449,12 @@ __global__ void __launch_bounds__((Body::kMaxWarps + 1) * 32, Body::kMinBlocks)
   const uint32_t total_tiles = p.counts ? p.counts[1] : p.total_tiles;
 
   if (warp == nc) {
-    if (lane == 0) producer_loop<W, Body::kLayout>(p, stripes, ptrs, ring, n_stripes, total_tiles);
+    if (lane == 0) producer_loop<W, Body::kLayout>(p, stripes, ptrs, coef, headers, ring, n_stripes, total_tiles);
     return;
   }
 
-  using Tile = std::conditional_t<Body::kLayout == kLayoutSymbol, SymTile<W>, PacketTile<W>>;
+  using Tile = std::conditional_t<Body::kLayout == kLayoutSymbol, SymTile<W, Body::kMaxOut>,
+                                  PacketTile<W, Body::kMaxOut>>;
   Tile tile;
   tile.ring = &ring;
   tile.status = p.status;
@@ -438,10 +468,13 @@ __global__ void __launch_bounds__((Body::kMaxWarps + 1) * 32, Body::kMinBlocks)
     tile.span = ring.slice / (uint32_t)W;
   }
   for (uint32_t t = blockIdx.x; t < total_tiles; t += gridDim.x) {
-    const StripeDesc& d = stripes[find_stripe(stripes, n_stripes, t)];
-    const TileGeom g = tile_geom(d, t - d.tile_begin, ring.slice, W);
-    tile.begin(d, g, ptrs + d.ptr_off);
-    Body::run(d, tile, coef);
+    // the tile's header is published by its first slot's full barrier
+    wait_or_fail(&ring.full[ring.s], ring.par, tile.failed, p.status, kDevErrTimeoutFull, p.wait_limit_ns);
+    if (tile.failed) break;
+    const TileHeader& h = headers[ring.s];
+    const TileOp op{h.read_mask, h.pmask, (int)h.k, (int)h.n_pos, (int)h.e, (int)h.m, (int)h.op};
+    tile.begin(h);
+    Body::run(op, tile, h.coef);  // bodies read h.coef before releasing the slot
     if (tile.failed) break;
   }
 }

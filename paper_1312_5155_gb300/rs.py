@@ -17,8 +17,9 @@ import threading
 PKG = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(PKG, "librs_gb300.so")
 
-RS_POLY, RS_VANDERMONDE, RS_CAUCHY = 0, 1, 2
-REALIZATIONS = {"poly": RS_POLY, "vandermonde": RS_VANDERMONDE, "cauchy": RS_CAUCHY}
+RS_POLY, RS_VANDERMONDE, RS_CAUCHY, RS_POLY_MATRIX, RS_POLY_BITMATRIX = 0, 1, 2, 3, 4
+REALIZATIONS = {"poly": RS_POLY, "vandermonde": RS_VANDERMONDE, "cauchy": RS_CAUCHY,
+                "poly_matrix": RS_POLY_MATRIX, "poly_bitmatrix": RS_POLY_BITMATRIX}
 RS_READ_MIN, RS_READ_ALL = 0, 1
 STATUS = {0: "RS_OK", 1: "RS_EINVAL", 2: "RS_ETOOMANY_ERASURES", 3: "RS_ENOMEM", 4: "RS_ECUDA",
           5: "RS_ETIMEOUT", 6: "RS_EUNSUPPORTED"}

@@ -216,24 +216,37 @@ class Server:
         return requests
 
     def _launch(self, slot, reqs, payloads, results):
+        """One batch on the slot's stream: inputs in (one copy of the k data
+        rows for an encode, of the whole stripe for a decode), one launch per
+        kernel group, outputs out (the m parity rows in one copy; the erased
+        rows of a decode one by one).  Block pointers are computed from the
+        arena base, so no tensor views are made per block."""
         torch = self.torch
         st = slot["stream"]
         ops = []
         with torch.cuda.stream(st):
             for r in reqs:
                 n, B = r.k + r.m, r.block_bytes
-                blocks = [self._block_view(r.off, b, B) for b in range(n)]
-                h2d, _ = io_blocks(r)
-                for b in h2d:
-                    blocks[b].copy_(payloads[r.rid][b], non_blocking=True)
-                ops.append((self.codes[(r.k, r.m)], r.op, r.erasures, blocks, B))
+                Bp = (B + 15) // 16 * 16
+                base = self.base + r.off
+                stripe = self.mem[r.off:r.off + n * Bp].view(n, Bp)
+                if r.op == "encode":
+                    stripe[:r.k, :B].copy_(payloads[r.rid][:r.k], non_blocking=True)
+                else:
+                    stripe[:, :B].copy_(payloads[r.rid], non_blocking=True)
+                ops.append((self.codes[(r.k, r.m)], r.op, r.erasures, [base + b * Bp for b in range(n)], B))
             slot["batch"].set(ops, stream=st)
             slot["batch"].launch(stream=st)
             if results is not None:
                 for r in reqs:
-                    _, d2h = io_blocks(r)
-                    for j, b in enumerate(d2h):
-                        results[r.rid][j].copy_(self._block_view(r.off, b, r.block_bytes), non_blocking=True)
+                    n, B = r.k + r.m, r.block_bytes
+                    Bp = (B + 15) // 16 * 16
+                    stripe = self.mem[r.off:r.off + n * Bp].view(n, Bp)
+                    if r.op == "encode":
+                        results[r.rid].copy_(stripe[r.k:, :B], non_blocking=True)
+                    else:
+                        for j, b in enumerate(r.erasures):
+                            results[r.rid][j].copy_(stripe[b, :B], non_blocking=True)
             slot["event"].record(st)
         slot["reqs"] = reqs
 

@@ -186,7 +186,7 @@ int mat_runtime(int k, const std::vector<uint32_t>& P, bool decode, const Decode
 
 template <int W, int K, int M, int KIND>
 int mat_fixed(bool decode, const DecodePlan* pl, uint8_t* blocks, size_t B, size_t pkt) {
-  constexpr bool kPacket = KIND == kKindCauchy;
+  constexpr bool kPacket = kind_layout(KIND) == 1;
   std::vector<const uint8_t*> in;
   std::vector<uint8_t*> out;
   if (!decode) {
@@ -222,6 +222,12 @@ int mat_runtime_m(int k, int m, const std::vector<uint32_t>& P, bool decode, con
 
 template <int KIND>
 int mat_fixed_dispatch(int w, int k, int m, bool decode, const DecodePlan* pl, uint8_t* b, size_t B, size_t pkt) {
+  if (KIND >= 3) {
+    if (w == 8 && k == 10 && m == 4) return mat_fixed<8, 10, 4, KIND>(decode, pl, b, B, pkt);
+    if (w == 8 && k == 6 && m == 3) return mat_fixed<8, 6, 3, KIND>(decode, pl, b, B, pkt);
+    if (w == 16 && k == 12 && m == 4) return mat_fixed<16, 12, 4, KIND>(decode, pl, b, B, pkt);
+    return -2;
+  }
   if (w == 8 && k == 6 && m == 3) return mat_fixed<8, 6, 3, KIND>(decode, pl, b, B, pkt);
   if (w == 8 && k == 10 && m == 4) return mat_fixed<8, 10, 4, KIND>(decode, pl, b, B, pkt);
   if (w == 8 && k == 12 && m == 4) return mat_fixed<8, 12, 4, KIND>(decode, pl, b, B, pkt);
@@ -235,16 +241,21 @@ int mat_fixed_dispatch(int w, int k, int m, bool decode, const DecodePlan* pl, u
 extern "C" {
 
 // Matrix realizations: kind 1 = Vandermonde (symbol layout), 2 = Cauchy
-// (packet layout, packet bytes pkt).  fixed: compile-time P kernels (only
-// for the registered codes), else runtime P.  er/e: decode when e > 0.
+// (packet layout, packet bytes pkt), 3 = polynomial code as a matrix
+// (symbol layout), 4 = its bit-matrix form (packet layout).  fixed:
+// compile-time P kernels (only for the registered codes), else runtime P.
+// er/e: decode when e > 0.
+static bool host_parity(int w, int k, int m, int kind, std::vector<uint32_t>& P) {
+  if (kind == 1) return vandermonde_parity_matrix(k, m, w, P);
+  if (kind == 2) cauchy_parity_matrix(k, m, w, P);
+  else poly_parity_matrix(k, m, w, P);
+  return true;
+}
+
 int emu_mat(int w, int k, int m, int kind, int fixed, const int* er, int e, int read_all, uint8_t* blocks, size_t B,
             size_t pkt) {
   std::vector<uint32_t> P;
-  if (kind == 1) {
-    if (!vandermonde_parity_matrix(k, m, w, P)) return -3;
-  } else {
-    cauchy_parity_matrix(k, m, w, P);
-  }
+  if (!host_parity(w, k, m, kind, P)) return -3;
   DecodePlan pl;
   const bool decode = e > 0;
   if (decode) {
@@ -252,9 +263,16 @@ int emu_mat(int w, int k, int m, int kind, int fixed, const int* er, int e, int 
     if (!make_matrix_decode_plan(k, m, w, P, er, e, read_all != 0, pl, err)) return -1;
   }
   const DecodePlan* plp = decode ? &pl : nullptr;
-  if (fixed) return kind == 1 ? mat_fixed_dispatch<1>(w, k, m, decode, plp, blocks, B, pkt)
-                              : mat_fixed_dispatch<2>(w, k, m, decode, plp, blocks, B, pkt);
-  const bool packet = kind == 2;
+  if (fixed) {
+    switch (kind) {
+      case 1: return mat_fixed_dispatch<1>(w, k, m, decode, plp, blocks, B, pkt);
+      case 2: return mat_fixed_dispatch<2>(w, k, m, decode, plp, blocks, B, pkt);
+      case 3: return mat_fixed_dispatch<3>(w, k, m, decode, plp, blocks, B, pkt);
+      case 4: return mat_fixed_dispatch<4>(w, k, m, decode, plp, blocks, B, pkt);
+    }
+    return -2;
+  }
+  const bool packet = kind == 2 || kind == 4;
   if (w == 8) return packet ? mat_runtime_m<8, true>(k, m, P, decode, plp, blocks, B, pkt)
                             : mat_runtime_m<8, false>(k, m, P, decode, plp, blocks, B, pkt);
   return packet ? mat_runtime_m<16, true>(k, m, P, decode, plp, blocks, B, pkt)
@@ -264,11 +282,7 @@ int emu_mat(int w, int k, int m, int kind, int fixed, const int* er, int e, int 
 // Host copy of the parity matrix the library builds (for the tests).
 int emu_parity_matrix(int w, int k, int m, int kind, uint32_t* out) {
   std::vector<uint32_t> P;
-  if (kind == 1) {
-    if (!vandermonde_parity_matrix(k, m, w, P)) return -3;
-  } else {
-    cauchy_parity_matrix(k, m, w, P);
-  }
+  if (!host_parity(w, k, m, kind, P)) return -3;
   for (size_t i = 0; i < P.size(); ++i) out[i] = P[i];
   return 0;
 }
@@ -280,6 +294,11 @@ int emu_fixed_parity_matrix(int w, int k, int m, int kind, uint32_t* out) {
       for (int j = 0; j < K; ++j) out[i * K + j] = mat.a[i][j];
     return 0;
   };
+  if (kind == 3) {
+    if (w == 8 && k == 10 && m == 4) return copy(ParityMatrix<8, 10, 4, 3>::value, 10, 4);
+    if (w == 16 && k == 12 && m == 4) return copy(ParityMatrix<16, 12, 4, 3>::value, 12, 4);
+    return -2;
+  }
   if (kind == 1) {
     if (w == 8 && k == 10 && m == 4) return copy(ParityMatrix<8, 10, 4, 1>::value, 10, 4);
     if (w == 8 && k == 20 && m == 4) return copy(ParityMatrix<8, 20, 4, 1>::value, 20, 4);

@@ -38,6 +38,10 @@ CASES = [
     ("cauchy", 16, 12, 4, 16 * 2048 * 2, 2048), ("cauchy", 8, 10, 4, 8 * 512 * 5, 512),
     ("cauchy", 8, 7, 5, 8 * 1024 * 3, 1024), ("cauchy", 16, 3, 2, 16 * 128 * 4, 128),
     ("cauchy", 8, 20, 4, 8 * 384 * 2, 384),
+    ("poly_matrix", 8, 10, 4, 1 << 20, None), ("poly_matrix", 8, 10, 4, 65536 + 37, None),
+    ("poly_matrix", 16, 12, 4, 100002, None), ("poly_matrix", 8, 7, 5, 50000, None),
+    ("poly_bitmatrix", 8, 10, 4, 8 * 2048 * 8, 2048), ("poly_bitmatrix", 8, 6, 3, 8 * 1024 * 3, 1024),
+    ("poly_bitmatrix", 16, 12, 4, 16 * 2048 * 2, 2048),
 ]
 
 
@@ -74,6 +78,20 @@ def test_decode_bit_exact(rs, real, w, k, m, B, pkt, read_mode):
         torch.cuda.synchronize()
         assert np.array_equal(to_host(buf, B), host), er
     assert code.poll_status() == 0
+
+
+def test_generator_matrix_form_equals_lfsr(rs):
+    """§6: the polynomial code through its generator matrix gives the LFSR's
+    bytes (and the same decode)."""
+    import torch
+    k, m, w, B = 10, 4, 8, (1 << 20) + 48
+    host = stripe(w, k, m, B)
+    a_buf, a_rows = device_blocks(host)
+    b_buf, b_rows = device_blocks(host)
+    rs.Code(k, m, w, "poly").encode(a_rows[:k], a_rows[k:], B)
+    rs.Code(k, m, w, "poly_matrix").encode(b_rows[:k], b_rows[k:], B)
+    torch.cuda.synchronize()
+    assert torch.equal(a_buf, b_buf)
 
 
 def test_cauchy_block_size_must_fit_packets(rs):

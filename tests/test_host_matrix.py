@@ -12,8 +12,9 @@ from paper_1312_5155_gb300 import inputs
 from tests.hostemu.build import build
 
 U8P = ctypes.POINTER(ctypes.c_uint8)
-KIND = {"vandermonde": 1, "cauchy": 2}
+KIND = {"vandermonde": 1, "cauchy": 2, "poly_matrix": 3, "poly_bitmatrix": 4}
 FIXED = {(8, 6, 3), (8, 10, 4), (8, 12, 4), (8, 20, 4), (16, 12, 4)}
+FIXED_POLY = {(8, 10, 4), (8, 6, 3), (16, 12, 4)}  # harness instantiations of kinds 3 and 4
 
 
 @pytest.fixture(scope="module")
@@ -33,17 +34,24 @@ def run(L, real, w, k, m, fixed, er, blocks, pkt, read_all=False):
     assert rc == 0, rc
 
 
-@pytest.mark.parametrize("real", ["vandermonde", "cauchy"])
+def oracle_parity(real, w, k, m):
+    if real == "vandermonde":
+        return O.vand_matrix(w, k, m)[k:]
+    if real == "cauchy":
+        return O.cauchy_matrix(w, k, m)
+    return O.polymat_matrix(w, k, m)
+
+
+@pytest.mark.parametrize("real", ["vandermonde", "cauchy", "poly_matrix"])
 @pytest.mark.parametrize("w,k,m", [(8, 10, 4), (8, 6, 3), (16, 12, 4), (8, 5, 7), (8, 20, 4), (16, 3, 2)])
 def test_host_parity_matrix_matches_oracle(emu, real, w, k, m):
     out = (ctypes.c_uint32 * (k * m))()
     assert emu.emu_parity_matrix(w, k, m, KIND[real], out) == 0
     got = np.array(list(out), dtype=np.uint32).reshape(m, k)
-    want = O.vand_matrix(w, k, m)[k:] if real == "vandermonde" else O.cauchy_matrix(w, k, m)
-    assert np.array_equal(got, want)
+    assert np.array_equal(got, oracle_parity(real, w, k, m))
 
 
-@pytest.mark.parametrize("real", ["vandermonde", "cauchy"])
+@pytest.mark.parametrize("real", ["vandermonde", "cauchy", "poly_matrix"])
 @pytest.mark.parametrize("w,k,m", [(8, 10, 4), (16, 12, 4), (8, 20, 4)])
 def test_compile_time_parity_matrix_matches_oracle(emu, real, w, k, m):
     out = (ctypes.c_uint32 * (k * m))()
@@ -51,8 +59,7 @@ def test_compile_time_parity_matrix_matches_oracle(emu, real, w, k, m):
     if rc == -2:
         pytest.skip("not exported by the harness")
     got = np.array(list(out), dtype=np.uint32).reshape(m, k)
-    want = O.vand_matrix(w, k, m)[k:] if real == "vandermonde" else O.cauchy_matrix(w, k, m)
-    assert np.array_equal(got, want)
+    assert np.array_equal(got, oracle_parity(real, w, k, m))
 
 
 def make_stripe(w, k, m, B, seed=3, stripe=0):
@@ -66,7 +73,15 @@ CASES = [("vandermonde", 8, 10, 4, 4096 + 48, 0), ("vandermonde", 8, 6, 3, 3000,
          ("vandermonde", 8, 20, 4, 1100, 0),
          ("cauchy", 8, 10, 4, 8 * 256 * 2, 256), ("cauchy", 8, 6, 3, 8 * 128 * 3, 128),
          ("cauchy", 16, 12, 4, 16 * 128 * 2, 128), ("cauchy", 8, 5, 7, 8 * 384, 384),
-         ("cauchy", 8, 20, 4, 8 * 128, 128)]
+         ("cauchy", 8, 20, 4, 8 * 128, 128),
+         ("poly_matrix", 8, 10, 4, 4096 + 48, 0), ("poly_matrix", 8, 6, 3, 3000, 0),
+         ("poly_matrix", 16, 12, 4, 8192 + 2, 0), ("poly_matrix", 8, 5, 7, 2048, 0),
+         ("poly_bitmatrix", 8, 10, 4, 8 * 256 * 2, 256), ("poly_bitmatrix", 8, 6, 3, 8 * 128 * 3, 128),
+         ("poly_bitmatrix", 16, 12, 4, 16 * 128 * 2, 128), ("poly_bitmatrix", 8, 5, 7, 8 * 384, 384)]
+
+
+def fixed_ok(real, w, k, m):
+    return (w, k, m) in (FIXED_POLY if real.startswith("poly") else FIXED)
 
 
 @pytest.mark.parametrize("real,w,k,m,B,pkt", CASES)
@@ -75,7 +90,7 @@ def test_encode_matches_oracle(emu, real, w, k, m, B, pkt):
     ref = base.copy()
     O.encode(real, w, k, m, ref, packet_bytes=pkt or 2048)
     for fixed in (False, True):
-        if fixed and (w, k, m) not in FIXED:
+        if fixed and not fixed_ok(real, w, k, m):
             continue
         got = base.copy()
         got[k:] = 0x44
@@ -93,7 +108,7 @@ def test_decode_seeded_patterns(emu, real, w, k, m, B, pkt, read_all):
         e = 1 + stripe % m
         er = inputs.erasure_pattern(11, stripe, n, e)
         for fixed in (False, True):
-            if fixed and (w, k, m) not in FIXED:
+            if fixed and not fixed_ok(real, w, k, m):
                 continue
             got = base.copy()
             got[er] = 0x99
@@ -101,7 +116,7 @@ def test_decode_seeded_patterns(emu, real, w, k, m, B, pkt, read_all):
             assert np.array_equal(got, base), (er, fixed)
 
 
-@pytest.mark.parametrize("real", ["vandermonde", "cauchy"])
+@pytest.mark.parametrize("real", ["vandermonde", "cauchy", "poly_matrix", "poly_bitmatrix"])
 def test_decode_every_pattern_rs_6_3(emu, real):
     w, k, m = 8, 6, 3
     pkt = 128
