@@ -156,6 +156,82 @@ struct PackedBits {
   }
 };
 
+// A runtime M x M decode matrix W in selector form.  Output row t is
+// evaluated as a polynomial in alpha over the bits of its entries,
+//   out_t = sum_c alpha^c Z_{t,c},   Z_{t,c} = sum_j [bit c of W[t][j]] S_j,
+// and Z_{t,c} is named by selector nibbles: nibble h of (t, c) holds in bit i
+// the bit c of W[t][4h + i].  Row t occupies kRowWords words; nibble
+// n = c * kChunks + h of the row sits at bits 4 * (n % 8) of word n / 8.
+// Every lane of a warp works on the same stripe, so the selectors are
+// warp-uniform and a branch on one never diverges.
+template <int W, int M>
+struct Selectors {
+  static constexpr int kChunks = (M + 3) / 4;
+  static constexpr int kRowWords = (W * kChunks + 7) / 8;
+  static constexpr int kWords = M * kRowWords;
+  static_assert(kWords == selector_words(M, W), "selector layout");
+  uint32_t w[kWords];
+  template <class Src>
+  RS_HD void load(const Src& src) {
+#pragma unroll
+    for (int i = 0; i < kWords; ++i) w[i] = src.word(i);
+  }
+  // Words of row t (runtime t; selects instead of indexing so that w stays
+  // in registers).
+  RS_HD void row(int t, uint32_t* r) const {
+#pragma unroll
+    for (int q = 0; q < kRowWords; ++q) {
+      uint32_t v = w[q];
+#pragma unroll
+      for (int u = 1; u < M; ++u) v = (t == u) ? w[u * kRowWords + q] : v;
+      r[q] = v;
+    }
+  }
+};
+
+// y ^= sum of S[i] over the set bits i of V, with y in rotation ROT (logical
+// plane b in register (b - ROT) mod W) and S in natural order.
+template <int W, int ROT, int NS, int V>
+RS_HD void xor_subset(uint32_t* y, const uint32_t (*S)[W]) {
+#pragma unroll
+  for (int b = 0; b < W; ++b) {
+    uint32_t z = y[((b - ROT) % W + W) % W];
+#pragma unroll
+    for (int i = 0; i < NS; ++i)
+      if ((V >> i) & 1) z ^= S[i][b];
+    y[((b - ROT) % W + W) % W] = z;
+  }
+}
+
+// y ^= the subset of S[0..NS-1] named by the 4-bit selector sel.
+template <int W, int ROT, int NS>
+RS_HD void xor_selected(uint32_t sel, uint32_t* y, const uint32_t (*S)[W]) {
+  switch (sel) {
+#define RSGB_SELECT_CASE(v)                                    \
+  case v:                                                      \
+    if constexpr (v < (1 << NS)) xor_subset<W, ROT, NS, v>(y, S); \
+    break;
+    RSGB_SELECT_CASE(1)
+    RSGB_SELECT_CASE(2)
+    RSGB_SELECT_CASE(3)
+    RSGB_SELECT_CASE(4)
+    RSGB_SELECT_CASE(5)
+    RSGB_SELECT_CASE(6)
+    RSGB_SELECT_CASE(7)
+    RSGB_SELECT_CASE(8)
+    RSGB_SELECT_CASE(9)
+    RSGB_SELECT_CASE(10)
+    RSGB_SELECT_CASE(11)
+    RSGB_SELECT_CASE(12)
+    RSGB_SELECT_CASE(13)
+    RSGB_SELECT_CASE(14)
+    RSGB_SELECT_CASE(15)
+#undef RSGB_SELECT_CASE
+    default:
+      break;
+  }
+}
+
 // acc[r] ^= sum_q M[r][q] * in_q ... for one input q: acc[r] ^= M[r][q] * x,
 // as sum over c of mask(r, q, c) & (alpha^c x).  x is clobbered.
 template <int W, int R, int Q>

@@ -237,7 +237,7 @@ rs_status prepare_decode(rs_code* c, const int* er, int e, void* const* blocks, 
   po.ptrs.clear();
   for (int b : pl.in_blocks) po.ptrs.push_back((uint64_t)(uintptr_t)blocks[b]);
   for (int b : pl.out_blocks) po.ptrs.push_back((uint64_t)(uintptr_t)blocks[b]);
-  po.coef = pack_decode_matrix(pl, c->w);
+  po.coef = pack_decode_selectors(pl, c->w);
   while (po.coef.size() % 4) po.coef.push_back(0u);  // keep every op's words 16-byte aligned
   return RS_OK;
 }

@@ -148,8 +148,8 @@ template <int W, int K, int M, int KIND, bool kTranspose>
 struct MatDecodeFixed {
   template <class Src, class Dst, class Coef>
   static RS_HD void run(uint64_t read_mask, int e, Src& src, Dst& dst, Coef& coef) {
-    PackedBits<W, M, M> wm;
-    wm.load(coef);
+    Selectors<W, M> sel;
+    sel.load(coef);
     uint32_t S[M][W];
 #pragma unroll
     for (int i = 0; i < M; ++i)
@@ -177,7 +177,7 @@ struct MatDecodeFixed {
         for (int b = 0; b < W; ++b) S[j][b] ^= x[b];
       }
     }
-    ApplyDispatch<W, M, kTranspose>::run(e, S, wm, dst);
+    apply_and_store<W, M, kTranspose>(e, S, sel, dst);
   }
 };
 
@@ -220,8 +220,8 @@ struct MatDecodeRuntime {
 #pragma unroll
       for (int b = 0; b < W; ++b) S[i][b] = 0;
     int in = 0;
-    PackedBits<W, M, M> wm;
-    wm.load(coef);
+    Selectors<W, M> sel;
+    sel.load(coef);
     for (int j = 0; j < k; ++j) {
       if (!((read_mask >> j) & 1ull)) continue;
       PackedBits<W, M, 1> col;
@@ -241,7 +241,7 @@ struct MatDecodeRuntime {
         for (int b = 0; b < W; ++b) S[j][b] ^= x[b];
       }
     }
-    ApplyDispatch<W, M, kTranspose>::run(e, S, wm, dst);
+    apply_and_store<W, M, kTranspose>(e, S, sel, dst);
   }
 };
 

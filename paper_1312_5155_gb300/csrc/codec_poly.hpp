@@ -2,8 +2,9 @@
 // bit-planes by one thread.  Host/device code; the caller supplies
 //   src.load(i, x)   : W words of input i (consumption order), as stored
 //   dst.store(t, x)  : W words of output t, as stored
-//   coef.word(i)     : word i of the runtime matrix W as packed bits
-//                      (PackedBits<W, M, M> layout, entry (t, j))
+//   dst.store(t, x)  : may be called with a runtime t
+//   coef.word(i)     : word i of the runtime matrix W in selector form
+//                      (Selectors<W, M> layout)
 #pragma once
 #include "bitslice.hpp"
 
@@ -138,61 +139,42 @@ RS_HD void horner_add(uint32_t (*S)[W], const uint32_t* x) {
   });
 }
 
-// out[t] = sum_j W[t][j] S_j for t < E, with W as packed bits (entry (t, j)).
-// For every syndrome j the chain alpha^c S_j (c = 0..W-1) is walked once and
-// shared by all outputs; each chain term costs one AND-XOR per plane.  E is a
-// compile-time count (the caller dispatches on the runtime e once), so no
-// per-term guards are emitted.  S is clobbered.
-template <int W, int M, int E>
-RS_HD void apply_runtime_matrix_e(uint32_t (*out)[W], uint32_t (*S)[W], const PackedBits<W, M, M>& wm) {
+// Erased outputs from the M syndromes: out_t = sum_j W[t][j] S_j for t < e,
+// one output at a time.  Each output is Horner's rule in alpha over the bits
+// of its row of W (top bit first): y = alpha * y + Z_{t,c}, where Z_{t,c} is
+// the XOR of the syndromes that the warp-uniform selector of (t, c) names.
+// The alpha steps are renamed, so an output costs (W - 1) folds of the top
+// plane plus one XOR per selected syndrome and plane, instead of W * M masked
+// XORs per plane.  After the last step y is in rotation W - 1 (logical plane b
+// in register (b + 1) mod W).
+template <int W, int M, bool kTranspose, class Dst>
+RS_HD void apply_and_store(int e, const uint32_t (*S)[W], const Selectors<W, M>& sel, Dst& dst) {
+  using Sel = Selectors<W, M>;
+#pragma unroll 1
+  for (int t = 0; t < e; ++t) {
+    uint32_t row[Sel::kRowWords];
+    sel.row(t, row);
+    uint32_t y[W];
 #pragma unroll
-  for (int t = 0; t < E; ++t)
+    for (int b = 0; b < W; ++b) y[b] = 0;
+    StaticFor<0, W>::run([&](auto CC) {
+      constexpr int cc = decltype(CC)::value;  // step; coefficient bit c = W - 1 - cc
+      constexpr int c = W - 1 - cc;
+      if constexpr (cc > 0) mul_alpha_renamed<W, cc - 1>(y);
+      StaticFor<0, Sel::kChunks>::run([&](auto H) {
+        constexpr int h = decltype(H)::value;
+        constexpr int n = c * Sel::kChunks + h;
+        constexpr int ns = (M - 4 * h < 4) ? M - 4 * h : 4;
+        xor_selected<W, cc, ns>((row[n >> 3] >> ((n & 7) * 4)) & 15u, y, S + 4 * h);
+      });
+    });
+    uint32_t o[W];
 #pragma unroll
-    for (int b = 0; b < W; ++b) out[t][b] = 0;
-#pragma unroll
-  for (int j = 0; j < M; ++j) {
-#pragma unroll
-    for (int c = 0; c < W; ++c) {
-#pragma unroll
-      for (int t = 0; t < E; ++t) {
-        const uint32_t mk = wm.mask(t, j, c);
-#pragma unroll
-        for (int b = 0; b < W; ++b) out[t][b] ^= S[j][b] & mk;
-      }
-      if (c + 1 < W) mul_alpha<W>(S[j]);
-    }
+    for (int b = 0; b < W; ++b) o[b] = y[(b + 1) % W];
+    if (kTranspose) transpose<W>(o);
+    dst.store(t, o);
   }
 }
-
-// Apply the runtime matrix for the e outputs and store them (symbols ->
-// planes back with kTranspose).
-template <int W, int M, int E, bool kTranspose, class Dst>
-RS_HD void apply_and_store(uint32_t (*S)[W], const PackedBits<W, M, M>& wm, Dst& dst) {
-  uint32_t out[E][W];
-  apply_runtime_matrix_e<W, M, E>(out, S, wm);
-#pragma unroll
-  for (int t = 0; t < E; ++t) {
-    if (kTranspose) transpose<W>(out[t]);
-    dst.store(t, out[t]);
-  }
-}
-
-template <int W, int M, bool kTranspose, int E = M>
-struct ApplyDispatch {
-  template <class Dst>
-  static RS_HD void run(int e, uint32_t (*S)[W], const PackedBits<W, M, M>& wm, Dst& dst) {
-    if (e == E) {
-      apply_and_store<W, M, E, kTranspose>(S, wm, dst);
-      return;
-    }
-    ApplyDispatch<W, M, kTranspose, E - 1>::run(e, S, wm, dst);
-  }
-};
-template <int W, int M, bool kTranspose>
-struct ApplyDispatch<W, M, kTranspose, 0> {
-  template <class Dst>
-  static RS_HD void run(int, uint32_t (*)[W], const PackedBits<W, M, M>&, Dst&) {}
-};
 
 template <int W, int M>
 struct PolyDecode {
@@ -200,8 +182,8 @@ struct PolyDecode {
   // case the next input (inputs ordered by descending position) holds it.
   template <class Src, class Dst, class Coef>
   static RS_HD void run(int n_pos, uint64_t read_mask, int e, Src& src, Dst& dst, Coef& coef) {
-    PackedBits<W, M, M> wm;  // loaded first: its latency hides behind Step 1
-    wm.load(coef);
+    Selectors<W, M> sel;  // loaded first: its latency hides behind Step 1
+    sel.load(coef);
     uint32_t S[M][W];
 #pragma unroll
     for (int j = 0; j < M; ++j)
@@ -227,7 +209,7 @@ struct PolyDecode {
       });
       pos -= W;
     }
-    ApplyDispatch<W, M, true>::run(e, S, wm, dst);
+    apply_and_store<W, M, true>(e, S, sel, dst);
   }
 };
 

@@ -23,6 +23,10 @@ namespace rsgb {
 constexpr int kMaxM = 8;        // parity blocks handled by the device path
 constexpr int kMaxBlocks = 64;  // k + m handled by the device path
 
+// Words of an m x m decode matrix over GF(2^w) in selector form: per row,
+// one nibble per (coefficient bit, chunk of four syndromes), eight a word.
+RS_CHD constexpr int selector_words(int m, int w) { return m * ((w * ((m + 3) / 4) + 7) / 8); }
+
 RS_CHD constexpr uint32_t prim_poly(int w) { return w == 8 ? 0x11Du : (w == 16 ? 0x1100Bu : 0u); }
 
 RS_CHD constexpr uint32_t gf_mul(uint32_t a, uint32_t b, int w) {

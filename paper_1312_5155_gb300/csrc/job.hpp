@@ -82,7 +82,7 @@ struct JobParams {
 // memory next to the tile's first slot before that slot is armed (so the
 // slot's full barrier publishes it).  Consumers copy what they need into
 // registers before they release that slot.
-constexpr int kHeaderCoefWords = (kMaxM * kMaxM * 16 + 31) / 32;
+constexpr int kHeaderCoefWords = selector_words(kMaxM, 16);
 struct alignas(16) TileHeader {
   uint64_t goff;
   uint64_t read_mask;

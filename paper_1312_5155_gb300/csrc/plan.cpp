@@ -171,12 +171,21 @@ std::vector<uint32_t> pack_bits(const uint32_t* a, int R, int Q, int w) {
   return out;
 }
 
-std::vector<uint32_t> pack_decode_matrix(const DecodePlan& pl, int w) {
+std::vector<uint32_t> pack_decode_selectors(const DecodePlan& pl, int w) {
   const int M = pl.M;
-  std::vector<uint32_t> a((size_t)M * M, 0u);
+  const int chunks = (M + 3) / 4;
+  const int row_words = (w * chunks + 7) / 8;
+  std::vector<uint32_t> out((size_t)selector_words(M, w), 0u);
   for (int t = 0; t < pl.e; ++t)
-    for (int j = 0; j < M; ++j) a[(size_t)t * M + j] = pl.W[t][j];
-  return pack_bits(a.data(), M, M, w);
+    for (int c = 0; c < w; ++c)
+      for (int h = 0; h < chunks; ++h) {
+        uint32_t nib = 0;
+        for (int i = 0; i < 4 && 4 * h + i < M; ++i)
+          if ((pl.W[t][4 * h + i] >> c) & 1u) nib |= 1u << i;
+        const int n = c * chunks + h;
+        out[(size_t)t * row_words + (n >> 3)] |= nib << ((n & 7) * 4);
+      }
+  return out;
 }
 
 std::vector<uint32_t> pack_columns(const std::vector<uint32_t>& P, int k, int m, int w) {

@@ -50,8 +50,12 @@ bool make_matrix_decode_plan(int k, int m, int w, const std::vector<uint32_t>& P
 // bit layout of PackedBits<W, R, Q>: entry (r, q) at bits [(q*R + r)*w, +w).
 std::vector<uint32_t> pack_bits(const uint32_t* a, int R, int Q, int w);
 
-// Words of the runtime decode matrix W (e used rows of the M x M slot).
-std::vector<uint32_t> pack_decode_matrix(const DecodePlan& pl, int w);
+// Words of the runtime decode matrix W (e used rows of the M x M slot) in
+// the device's selector form: for row t, coefficient bit c and chunk h of
+// four syndromes, a nibble whose bit i is bit c of W[t][4h + i]; nibble
+// n = c * ceil(M/4) + h of row t at bits 4 * (n % 8) of word
+// t * ceil(w * ceil(M/4) / 8) + n / 8.
+std::vector<uint32_t> pack_decode_selectors(const DecodePlan& pl, int w);
 
 // Words of P's columns for the runtime-P kernels: column j (entries
 // P[0..m-1][j]) occupies column_words(m, w) consecutive words.

@@ -105,6 +105,45 @@ __device__ __forceinline__ void wait_or_fail(uint64_t* bar, uint32_t par, bool& 
   }
 }
 
+// The last n < 16 bytes of a block, read from global memory as a zero-padded
+// 16-byte chunk.  A rolled loop: the path is cold (one chunk per block at
+// most) and is instantiated at every unrolled input load, so it is kept
+// small to leave the instruction cache to the arithmetic.
+__device__ __forceinline__ uint4 ragged_load(const uint8_t* g, uint32_t n) {
+  uint32_t w0 = 0, w1 = 0, w2 = 0, w3 = 0;
+#pragma unroll 1
+  for (int t = (int)n - 1; t >= 0; --t) {
+    w3 = (w3 << 8) | (w2 >> 24);
+    w2 = (w2 << 8) | (w1 >> 24);
+    w1 = (w1 << 8) | (w0 >> 24);
+    w0 = (w0 << 8) | g[t];
+  }
+  return make_uint4(w0, w1, w2, w3);
+}
+
+// Store the first n < 16 bytes of a chunk (the ragged end of a block).
+__device__ __forceinline__ void ragged_store(uint8_t* g, uint4 v, uint32_t n) {
+  uint32_t a = v.x, b = v.y, c = v.z, d = v.w;
+#pragma unroll 1
+  for (uint32_t t = 0; t < n; ++t) {
+    g[t] = (uint8_t)a;
+    a = (a >> 8) | (b << 24);
+    b = (b >> 8) | (c << 24);
+    c = (c >> 8) | (d << 24);
+    d >>= 8;
+  }
+}
+
+// outp[t] for a runtime t without indexing the register array (which would
+// put it in local memory); folds to outp[t] when t is a constant.
+template <int MO>
+__device__ __forceinline__ uint64_t select_out(const uint64_t (&outp)[MO], int t) {
+  uint64_t p = outp[0];
+#pragma unroll
+  for (int u = 1; u < MO; ++u) p = (t == u) ? outp[u] : p;
+  return p;
+}
+
 // ------------------------------------------------------ consumer tile views
 template <int W, int MO>
 struct SymTile {
@@ -145,15 +184,7 @@ struct SymTile {
         if (co + 16u <= len16) {
           v = *reinterpret_cast<const uint4*>(slot + co);
         } else if (co < len) {
-          // ragged end of the block (< 16 bytes): read it from global memory
-          const uint8_t* g = reinterpret_cast<const uint8_t*>(ptrs[i]) + goff + co;
-          uint8_t b[16];
-#pragma unroll
-          for (int t = 0; t < 16; ++t) b[t] = (co + (uint32_t)t < len) ? g[t] : 0;
-          v.x = b[0] | (b[1] << 8) | (b[2] << 16) | ((uint32_t)b[3] << 24);
-          v.y = b[4] | (b[5] << 8) | (b[6] << 16) | ((uint32_t)b[7] << 24);
-          v.z = b[8] | (b[9] << 8) | (b[10] << 16) | ((uint32_t)b[11] << 24);
-          v.w = b[12] | (b[13] << 8) | (b[14] << 16) | ((uint32_t)b[15] << 24);
+          v = ragged_load(reinterpret_cast<const uint8_t*>(ptrs[i]) + goff + co, min(len - co, 16u));
         }
       }
       x[4 * c + 0] = v.x;
@@ -166,7 +197,7 @@ struct SymTile {
 
   __device__ __forceinline__ void store(int t, const uint32_t* x) {
     if (failed) return;
-    uint8_t* out = reinterpret_cast<uint8_t*>(outp[t]) + goff;
+    uint8_t* out = reinterpret_cast<uint8_t*>(select_out(outp, t)) + goff;
 #pragma unroll
     for (int c = 0; c < W / 4; ++c) {
       const uint32_t co = seg + (uint32_t)c * 512u + lane * 16u;
@@ -174,8 +205,7 @@ struct SymTile {
       if (co + 16u <= len) {
         *reinterpret_cast<uint4*>(out + co) = v;
       } else if (co < len) {
-        const uint32_t wv[4] = {v.x, v.y, v.z, v.w};
-        for (uint32_t t2 = 0; co + t2 < len; ++t2) out[co + t2] = (uint8_t)(wv[t2 >> 2] >> (8 * (t2 & 3)));
+        ragged_store(out + co, v, len - co);
       }
     }
   }
@@ -220,13 +250,13 @@ struct PacketTile {
 
   __device__ __forceinline__ void store(int t, const uint32_t* x) {
     if (failed) return;
-    uint8_t* out = reinterpret_cast<uint8_t*>(outp[t]) + goff + span_off + 4u * word;
+    uint8_t* out = reinterpret_cast<uint8_t*>(select_out(outp, t)) + goff + span_off + 4u * word;
 #pragma unroll
     for (int c = 0; c < W; ++c) *reinterpret_cast<uint32_t*>(out + (size_t)c * P) = x[c];
   }
 };
 
-// Runtime decode matrix W as packed bits (PackedBits<W, M, M> layout).
+// Runtime decode matrix W in selector form (Selectors<W, M> layout).
 struct CoefWords {
   const uint32_t* base;
   __device__ __forceinline__ uint32_t word(int i) const { return base[i]; }
@@ -385,7 +415,7 @@ __device__ __forceinline__ void producer_loop(const JobParams& p, const StripeDe
         h.e = d.e;
         for (int t = 0; t < kMaxM; ++t) h.outp[t] = t < (int)d.n_out ? ip[d.n_in + t] : 0ull;
         if (d.op == kOpDecode || d.op == kOpMatDecode) {
-          const int words = ((int)d.m * (int)d.m * W + 31) / 32;
+          const int words = selector_words((int)d.m, W);
           for (int q = 0; q < words; ++q) h.coef[q] = coef[d.coef_off + q];
         }
       }

@@ -47,7 +47,7 @@ struct HostTile {
 
 struct HostCoef {
   std::vector<uint32_t> words;
-  explicit HostCoef(const DecodePlan* pl, int w) : words(pack_decode_matrix(*pl, w)) {}
+  explicit HostCoef(const DecodePlan* pl, int w) : words(pack_decode_selectors(*pl, w)) {}
   uint32_t word(int i) const { return words[i]; }
 };
 
