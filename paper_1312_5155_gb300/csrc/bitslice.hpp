@@ -189,27 +189,33 @@ struct Selectors {
   }
 };
 
-// y ^= sum of S[i] over the set bits i of V, with y in rotation ROT (logical
-// plane b in register (b - ROT) mod W) and S in natural order.
+// y ^= sum of S[i] over the set bits i of V (V < 2^NS), with y in rotation
+// ROT (logical plane b in register (b - ROT) mod W) and S in natural order.
+// P holds the pair sums S[0]^S[1] and S[2]^S[3], so any subset of four is
+// at most two terms and every plane costs one 3-input XOR.
 template <int W, int ROT, int NS, int V>
-RS_HD void xor_subset(uint32_t* y, const uint32_t (*S)[W]) {
+RS_HD void xor_subset(uint32_t* y, const uint32_t (*S)[W], const uint32_t (*P)[W]) {
+  constexpr int lo = V & 3, hi = (V >> 2) & 3;
 #pragma unroll
   for (int b = 0; b < W; ++b) {
     uint32_t z = y[((b - ROT) % W + W) % W];
-#pragma unroll
-    for (int i = 0; i < NS; ++i)
-      if ((V >> i) & 1) z ^= S[i][b];
+    if constexpr (lo == 1) z ^= S[0][b];
+    if constexpr (lo == 2) z ^= S[1][b];
+    if constexpr (lo == 3) z ^= P[0][b];
+    if constexpr (hi == 1) z ^= S[2][b];
+    if constexpr (hi == 2) z ^= S[3][b];
+    if constexpr (hi == 3) z ^= P[1][b];
     y[((b - ROT) % W + W) % W] = z;
   }
 }
 
 // y ^= the subset of S[0..NS-1] named by the 4-bit selector sel.
 template <int W, int ROT, int NS>
-RS_HD void xor_selected(uint32_t sel, uint32_t* y, const uint32_t (*S)[W]) {
+RS_HD void xor_selected(uint32_t sel, uint32_t* y, const uint32_t (*S)[W], const uint32_t (*P)[W]) {
   switch (sel) {
-#define RSGB_SELECT_CASE(v)                                    \
-  case v:                                                      \
-    if constexpr (v < (1 << NS)) xor_subset<W, ROT, NS, v>(y, S); \
+#define RSGB_SELECT_CASE(v)                                           \
+  case v:                                                             \
+    if constexpr (v < (1 << NS)) xor_subset<W, ROT, NS, v>(y, S, P); \
     break;
     RSGB_SELECT_CASE(1)
     RSGB_SELECT_CASE(2)

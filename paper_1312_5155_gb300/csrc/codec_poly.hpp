@@ -126,23 +126,38 @@ RS_HD void horner_mul(uint32_t (*S)[W]) {
   });
 }
 
-// Add input x (planes) into every syndrome at rotation state after step s.
+// One Horner step with an input: S_j = alpha^j S_j + x for every j.  The
+// last alpha step of each syndrome is fused with the addition, so its fold
+// of the top plane and the input's plane cost one 3-input XOR.
 template <int W, int M, int s>
-RS_HD void horner_add(uint32_t (*S)[W], const uint32_t* x) {
+RS_HD void horner_mul_add(uint32_t (*S)[W], const uint32_t* x) {
+  constexpr uint32_t low = prim_poly(W) & ((1u << W) - 1u);
 #pragma unroll
   for (int b = 0; b < W; ++b) S[0][b] ^= x[b];
   StaticFor<1, M>::run([&](auto J) {
     constexpr int j = decltype(J)::value;
-    constexpr int rot = (j * (s + 1)) % W;
+    StaticFor<0, j - 1>::run([&](auto T) {
+      mul_alpha_renamed<W, (j * s + decltype(T)::value) % W>(S[j]);
+    });
+    constexpr int np = j * s + j;               // rotation after the fused step
+    constexpr int top = ((0 - np) % W + W) % W;  // register of new logical plane 0
 #pragma unroll
-    for (int b = 0; b < W; ++b) S[j][((b - rot) % W + W) % W] ^= x[b];
+    for (int b = 1; b < W; ++b) {
+      const int ph = ((b - np) % W + W) % W;
+      if ((low >> b) & 1u)
+        S[j][ph] ^= S[j][top] ^ x[b];
+      else
+        S[j][ph] ^= x[b];
+    }
+    S[j][top] ^= x[0];  // after the folds, which read the old top plane
   });
 }
 
 // Erased outputs from the M syndromes: out_t = sum_j W[t][j] S_j for t < e,
 // one output at a time.  Each output is Horner's rule in alpha over the bits
 // of its row of W (top bit first): y = alpha * y + Z_{t,c}, where Z_{t,c} is
-// the XOR of the syndromes that the warp-uniform selector of (t, c) names.
+// the XOR of the syndromes that the warp-uniform selector of (t, c) names
+// (at most two terms per chunk of four, using precomputed pair sums).
 // The alpha steps are renamed, so an output costs (W - 1) folds of the top
 // plane plus one XOR per selected syndrome and plane, instead of W * M masked
 // XORs per plane.  After the last step y is in rotation W - 1 (logical plane b
@@ -150,6 +165,15 @@ RS_HD void horner_add(uint32_t (*S)[W], const uint32_t* x) {
 template <int W, int M, bool kTranspose, class Dst>
 RS_HD void apply_and_store(int e, const uint32_t (*S)[W], const Selectors<W, M>& sel, Dst& dst) {
   using Sel = Selectors<W, M>;
+  // pair sums per chunk of four syndromes (entries a chunk lacks stay unused)
+  uint32_t P[Sel::kChunks][2][W];
+#pragma unroll
+  for (int h = 0; h < Sel::kChunks; ++h)
+#pragma unroll
+    for (int b = 0; b < W; ++b) {
+      if (4 * h + 1 < M) P[h][0][b] = S[4 * h][b] ^ S[4 * h + 1][b];
+      if (4 * h + 3 < M) P[h][1][b] = S[4 * h + 2][b] ^ S[4 * h + 3][b];
+    }
 #pragma unroll 1
   for (int t = 0; t < e; ++t) {
     uint32_t row[Sel::kRowWords];
@@ -165,7 +189,7 @@ RS_HD void apply_and_store(int e, const uint32_t (*S)[W], const Selectors<W, M>&
         constexpr int h = decltype(H)::value;
         constexpr int n = c * Sel::kChunks + h;
         constexpr int ns = (M - 4 * h < 4) ? M - 4 * h : 4;
-        xor_selected<W, cc, ns>((row[n >> 3] >> ((n & 7) * 4)) & 15u, y, S + 4 * h);
+        xor_selected<W, cc, ns>((row[n >> 3] >> ((n & 7) * 4)) & 15u, y, S + 4 * h, P[h]);
       });
     });
     uint32_t o[W];
@@ -199,12 +223,13 @@ struct PolyDecode {
       StaticFor<0, W>::run([&](auto St) {
         constexpr int st = decltype(St)::value;
         const int p = pos - st;
-        horner_mul<W, M, st>(S);
         if (p < n_pos && ((read_mask >> p) & 1ull)) {
           uint32_t x[W];
           src.load(i++, x);
           transpose<W>(x);
-          horner_add<W, M, st>(S, x);
+          horner_mul_add<W, M, st>(S, x);
+        } else {
+          horner_mul<W, M, st>(S);
         }
       });
       pos -= W;

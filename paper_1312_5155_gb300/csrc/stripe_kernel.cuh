@@ -158,12 +158,15 @@ struct SymTile {
   int* status;
   unsigned long long limit;
   bool failed;
+  bool whole;      // this thread's chunks are all full 16-byte chunks in the slot
 
   __device__ __forceinline__ void begin(const TileHeader& h) {
     ptrs = reinterpret_cast<const uint64_t*>(h.ptrs);
     n_in = h.n_in;
     goff = h.goff;
     len = h.len;
+    // every chunk of this thread lies in the bulk-copied part of the slot
+    whole = seg + (uint32_t)(W / 4 - 1) * 512u + lane * 16u + 16u <= (len & ~15u);
 #pragma unroll
     for (int t = 0; t < MO; ++t) outp[t] = h.outp[t];
   }
@@ -174,23 +177,34 @@ struct SymTile {
     const uint32_t s = r.s, par = r.par;
     r.advance();
     wait_or_fail(&r.full[s], par, failed, status, kDevErrTimeoutFull, limit);
+    // After a timed-out wait the slot may hold stale bytes; they are read
+    // anyway (the addresses are valid) and store() writes nothing.
     const uint8_t* slot = r.slots + (size_t)s * r.slice;
-    const uint32_t len16 = len & ~15u;
+    if (whole) {
 #pragma unroll
-    for (int c = 0; c < W / 4; ++c) {
-      const uint32_t co = seg + (uint32_t)c * 512u + lane * 16u;
-      uint4 v = make_uint4(0, 0, 0, 0);
-      if (!failed) {
+      for (int c = 0; c < W / 4; ++c) {
+        const uint4 v = *reinterpret_cast<const uint4*>(slot + seg + (uint32_t)c * 512u + lane * 16u);
+        x[4 * c + 0] = v.x;
+        x[4 * c + 1] = v.y;
+        x[4 * c + 2] = v.z;
+        x[4 * c + 3] = v.w;
+      }
+    } else {
+      const uint32_t len16 = len & ~15u;
+#pragma unroll
+      for (int c = 0; c < W / 4; ++c) {
+        const uint32_t co = seg + (uint32_t)c * 512u + lane * 16u;
+        uint4 v = make_uint4(0, 0, 0, 0);
         if (co + 16u <= len16) {
           v = *reinterpret_cast<const uint4*>(slot + co);
         } else if (co < len) {
           v = ragged_load(reinterpret_cast<const uint8_t*>(ptrs[i]) + goff + co, min(len - co, 16u));
         }
+        x[4 * c + 0] = v.x;
+        x[4 * c + 1] = v.y;
+        x[4 * c + 2] = v.z;
+        x[4 * c + 3] = v.w;
       }
-      x[4 * c + 0] = v.x;
-      x[4 * c + 1] = v.y;
-      x[4 * c + 2] = v.z;
-      x[4 * c + 3] = v.w;
     }
     mbar_arrive(&r.empty[s]);
   }
@@ -243,8 +257,8 @@ struct PacketTile {
     wait_or_fail(&r.full[s], par, failed, status, kDevErrTimeoutFull, limit);
     const uint8_t* slot = r.slots + (size_t)s * r.slice;
 #pragma unroll
-    for (int c = 0; c < W; ++c)
-      x[c] = failed ? 0u : *reinterpret_cast<const uint32_t*>(slot + (size_t)c * span + 4u * word);
+    for (int c = 0; c < W; ++c)  // stale after a timed-out wait; store() then writes nothing
+      x[c] = *reinterpret_cast<const uint32_t*>(slot + (size_t)c * span + 4u * word);
     mbar_arrive(&r.empty[s]);
   }
 
