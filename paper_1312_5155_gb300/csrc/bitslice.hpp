@@ -60,6 +60,19 @@ RS_HD uint32_t shr_fma(uint32_t x) {
 #endif
 }
 
+// (a & m) | (b & ~m) as one 3-input logic instruction (truth table 0xE4 over
+// a = 0xF0, b = 0xCC, m = 0xAA); written out because the compiler otherwise
+// splits it in two.
+RS_HD uint32_t bit_select(uint32_t a, uint32_t b, uint32_t m) {
+#if defined(__CUDA_ARCH__)
+  uint32_t d;
+  asm("lop3.b32 %0, %1, %2, %3, 0xE4;" : "=r"(d) : "r"(a), "r"(b), "r"(m));
+  return d;
+#else
+  return (a & m) | (b & ~m);
+#endif
+}
+
 // x[i], x[i+D] for all i with bit D clear: exchange the bits of x[i] above
 // the mask with the bits of x[i+D] below it.
 template <int N, int D, int S, uint32_t MASK>
@@ -76,8 +89,8 @@ RS_HD void swap_round(uint32_t* x) {
         continue;
       }
 #endif
-      x[i] = (lo & MASK) | (shl_fma<S>(hi) & ~MASK);
-      x[i + D] = (shr_fma<S>(lo) & MASK) | (hi & ~MASK);
+      x[i] = bit_select(lo, shl_fma<S>(hi), MASK);
+      x[i + D] = bit_select(shr_fma<S>(lo), hi, MASK);
     }
   }
 }
@@ -209,9 +222,66 @@ RS_HD void xor_subset(uint32_t* y, const uint32_t (*S)[W], const uint32_t (*P)[W
   }
 }
 
+#if defined(__CUDA_ARCH__)
+RS_CHD constexpr int rotated(int b, int rot, int w) { return ((b - rot) % w + w) % w; }
+
+// GF(2^8) form of xor_selected with a warp-uniform jump table (brx.idx.uni)
+// over the 16 selector values; written out because the compiler lowers the
+// switch to a tree of compares.  Operand order: y planes %0-%7 (logical,
+// so the rotation is in the operand list), S0..S3 %8-%39, the pair sums
+// %40-%55, sel %56.  Operands of syndromes beyond NS feed only unreachable
+// cases and are bound to S0.
+template <int ROT, int NS>
+__device__ __forceinline__ void xor_selected_w8(uint32_t sel, uint32_t* y, const uint32_t (*S)[8],
+                                                const uint32_t (*P)[8]) {
+  const uint32_t* s0 = S[0];
+  const uint32_t* s1 = NS > 1 ? S[1] : S[0];
+  const uint32_t* s2 = NS > 2 ? S[2] : S[0];
+  const uint32_t* s3 = NS > 3 ? S[3] : S[0];
+  const uint32_t* p0 = NS > 1 ? P[0] : S[0];
+  const uint32_t* p1 = NS > 3 ? P[1] : S[0];
+  asm("{\n\t"
+      "ts: .branchtargets L0, L1, L2, L3, L4, L5, L6, L7, L8, L9, L10, L11, L12, L13, L14, L15;\n\t"
+      "brx.idx.uni %56, ts;\n"
+      "L0: bra.uni END;\n"
+      "L1: xor.b32 %0, %0, %8; xor.b32 %1, %1, %9; xor.b32 %2, %2, %10; xor.b32 %3, %3, %11; xor.b32 %4, %4, %12; xor.b32 %5, %5, %13; xor.b32 %6, %6, %14; xor.b32 %7, %7, %15; bra.uni END;\n"
+      "L2: xor.b32 %0, %0, %16; xor.b32 %1, %1, %17; xor.b32 %2, %2, %18; xor.b32 %3, %3, %19; xor.b32 %4, %4, %20; xor.b32 %5, %5, %21; xor.b32 %6, %6, %22; xor.b32 %7, %7, %23; bra.uni END;\n"
+      "L3: xor.b32 %0, %0, %40; xor.b32 %1, %1, %41; xor.b32 %2, %2, %42; xor.b32 %3, %3, %43; xor.b32 %4, %4, %44; xor.b32 %5, %5, %45; xor.b32 %6, %6, %46; xor.b32 %7, %7, %47; bra.uni END;\n"
+      "L4: xor.b32 %0, %0, %24; xor.b32 %1, %1, %25; xor.b32 %2, %2, %26; xor.b32 %3, %3, %27; xor.b32 %4, %4, %28; xor.b32 %5, %5, %29; xor.b32 %6, %6, %30; xor.b32 %7, %7, %31; bra.uni END;\n"
+      "L5: lop3.b32 %0, %0, %8, %24, 0x96; lop3.b32 %1, %1, %9, %25, 0x96; lop3.b32 %2, %2, %10, %26, 0x96; lop3.b32 %3, %3, %11, %27, 0x96; lop3.b32 %4, %4, %12, %28, 0x96; lop3.b32 %5, %5, %13, %29, 0x96; lop3.b32 %6, %6, %14, %30, 0x96; lop3.b32 %7, %7, %15, %31, 0x96; bra.uni END;\n"
+      "L6: lop3.b32 %0, %0, %16, %24, 0x96; lop3.b32 %1, %1, %17, %25, 0x96; lop3.b32 %2, %2, %18, %26, 0x96; lop3.b32 %3, %3, %19, %27, 0x96; lop3.b32 %4, %4, %20, %28, 0x96; lop3.b32 %5, %5, %21, %29, 0x96; lop3.b32 %6, %6, %22, %30, 0x96; lop3.b32 %7, %7, %23, %31, 0x96; bra.uni END;\n"
+      "L7: lop3.b32 %0, %0, %40, %24, 0x96; lop3.b32 %1, %1, %41, %25, 0x96; lop3.b32 %2, %2, %42, %26, 0x96; lop3.b32 %3, %3, %43, %27, 0x96; lop3.b32 %4, %4, %44, %28, 0x96; lop3.b32 %5, %5, %45, %29, 0x96; lop3.b32 %6, %6, %46, %30, 0x96; lop3.b32 %7, %7, %47, %31, 0x96; bra.uni END;\n"
+      "L8: xor.b32 %0, %0, %32; xor.b32 %1, %1, %33; xor.b32 %2, %2, %34; xor.b32 %3, %3, %35; xor.b32 %4, %4, %36; xor.b32 %5, %5, %37; xor.b32 %6, %6, %38; xor.b32 %7, %7, %39; bra.uni END;\n"
+      "L9: lop3.b32 %0, %0, %8, %32, 0x96; lop3.b32 %1, %1, %9, %33, 0x96; lop3.b32 %2, %2, %10, %34, 0x96; lop3.b32 %3, %3, %11, %35, 0x96; lop3.b32 %4, %4, %12, %36, 0x96; lop3.b32 %5, %5, %13, %37, 0x96; lop3.b32 %6, %6, %14, %38, 0x96; lop3.b32 %7, %7, %15, %39, 0x96; bra.uni END;\n"
+      "L10: lop3.b32 %0, %0, %16, %32, 0x96; lop3.b32 %1, %1, %17, %33, 0x96; lop3.b32 %2, %2, %18, %34, 0x96; lop3.b32 %3, %3, %19, %35, 0x96; lop3.b32 %4, %4, %20, %36, 0x96; lop3.b32 %5, %5, %21, %37, 0x96; lop3.b32 %6, %6, %22, %38, 0x96; lop3.b32 %7, %7, %23, %39, 0x96; bra.uni END;\n"
+      "L11: lop3.b32 %0, %0, %40, %32, 0x96; lop3.b32 %1, %1, %41, %33, 0x96; lop3.b32 %2, %2, %42, %34, 0x96; lop3.b32 %3, %3, %43, %35, 0x96; lop3.b32 %4, %4, %44, %36, 0x96; lop3.b32 %5, %5, %45, %37, 0x96; lop3.b32 %6, %6, %46, %38, 0x96; lop3.b32 %7, %7, %47, %39, 0x96; bra.uni END;\n"
+      "L12: xor.b32 %0, %0, %48; xor.b32 %1, %1, %49; xor.b32 %2, %2, %50; xor.b32 %3, %3, %51; xor.b32 %4, %4, %52; xor.b32 %5, %5, %53; xor.b32 %6, %6, %54; xor.b32 %7, %7, %55; bra.uni END;\n"
+      "L13: lop3.b32 %0, %0, %8, %48, 0x96; lop3.b32 %1, %1, %9, %49, 0x96; lop3.b32 %2, %2, %10, %50, 0x96; lop3.b32 %3, %3, %11, %51, 0x96; lop3.b32 %4, %4, %12, %52, 0x96; lop3.b32 %5, %5, %13, %53, 0x96; lop3.b32 %6, %6, %14, %54, 0x96; lop3.b32 %7, %7, %15, %55, 0x96; bra.uni END;\n"
+      "L14: lop3.b32 %0, %0, %16, %48, 0x96; lop3.b32 %1, %1, %17, %49, 0x96; lop3.b32 %2, %2, %18, %50, 0x96; lop3.b32 %3, %3, %19, %51, 0x96; lop3.b32 %4, %4, %20, %52, 0x96; lop3.b32 %5, %5, %21, %53, 0x96; lop3.b32 %6, %6, %22, %54, 0x96; lop3.b32 %7, %7, %23, %55, 0x96; bra.uni END;\n"
+      "L15: lop3.b32 %0, %0, %40, %48, 0x96; lop3.b32 %1, %1, %41, %49, 0x96; lop3.b32 %2, %2, %42, %50, 0x96; lop3.b32 %3, %3, %43, %51, 0x96; lop3.b32 %4, %4, %44, %52, 0x96; lop3.b32 %5, %5, %45, %53, 0x96; lop3.b32 %6, %6, %46, %54, 0x96; lop3.b32 %7, %7, %47, %55, 0x96;\n"
+      "END:\n\t}"
+      : "+r"(y[rotated(0, ROT, 8)]), "+r"(y[rotated(1, ROT, 8)]), "+r"(y[rotated(2, ROT, 8)]),
+        "+r"(y[rotated(3, ROT, 8)]), "+r"(y[rotated(4, ROT, 8)]), "+r"(y[rotated(5, ROT, 8)]),
+        "+r"(y[rotated(6, ROT, 8)]), "+r"(y[rotated(7, ROT, 8)])
+      : "r"(s0[0]), "r"(s0[1]), "r"(s0[2]), "r"(s0[3]), "r"(s0[4]), "r"(s0[5]), "r"(s0[6]), "r"(s0[7]),
+        "r"(s1[0]), "r"(s1[1]), "r"(s1[2]), "r"(s1[3]), "r"(s1[4]), "r"(s1[5]), "r"(s1[6]), "r"(s1[7]),
+        "r"(s2[0]), "r"(s2[1]), "r"(s2[2]), "r"(s2[3]), "r"(s2[4]), "r"(s2[5]), "r"(s2[6]), "r"(s2[7]),
+        "r"(s3[0]), "r"(s3[1]), "r"(s3[2]), "r"(s3[3]), "r"(s3[4]), "r"(s3[5]), "r"(s3[6]), "r"(s3[7]),
+        "r"(p0[0]), "r"(p0[1]), "r"(p0[2]), "r"(p0[3]), "r"(p0[4]), "r"(p0[5]), "r"(p0[6]), "r"(p0[7]),
+        "r"(p1[0]), "r"(p1[1]), "r"(p1[2]), "r"(p1[3]), "r"(p1[4]), "r"(p1[5]), "r"(p1[6]), "r"(p1[7]),
+        "r"(sel));
+}
+#endif
+
 // y ^= the subset of S[0..NS-1] named by the 4-bit selector sel.
 template <int W, int ROT, int NS>
 RS_HD void xor_selected(uint32_t sel, uint32_t* y, const uint32_t (*S)[W], const uint32_t (*P)[W]) {
+#if defined(__CUDA_ARCH__)
+  if constexpr (W == 8) {
+    xor_selected_w8<ROT, NS>(sel, y, S, P);
+    return;
+  }
+#endif
   switch (sel) {
 #define RSGB_SELECT_CASE(v)                                           \
   case v:                                                             \
