@@ -1,9 +1,11 @@
 // Persistent, TMA-staged stripe kernel (sm_103a).
 //
 // CTA = NC consumer warps + 1 producer warp.  The producer's lane 0 walks the
-// CTA's tiles (global tile t = blockIdx.x + i * gridDim.x over all stripes of
-// the launch) and, for every input block of the tile's stripe, issues 1-D
-// bulk copies (cp.async.bulk) of the tile's slice of that block into the
+// CTA's tiles (a contiguous run of the launch's global tile indices, so
+// consecutive tiles almost always belong to the same stripe and the stripe's
+// descriptor stays in registers) and, for every input block of the tile's
+// stripe, issues 1-D bulk copies (cp.async.bulk) of the tile's slice of that
+// block into the
 // next slot of a shared-memory ring; the slot's full mbarrier counts the
 // bytes.  Consumer warps walk the same tile sequence; every thread owns 32
 // columns of the tile, reads them from the slot, runs the codec ("body") on
@@ -20,7 +22,8 @@
 //   packet (§2.3 bit-matrix layout): a block is super-packets of W packets of
 //     P bytes; packet c holds bit c of the super-packet's 8P symbols.  A tile
 //     covers a span of NC*128 bytes at the same offset of the W packets of one
-//     super-packet (W bulk copies per block); lane l of warp v owns 32-bit
+//     super-packet (W bulk copies per block, one when the span is a whole
+//     packet and the W packets are contiguous); lane l of warp v owns 32-bit
 //     word v*32 + l of the span in each packet, which are already the W
 //     bit-planes of 32 symbols.
 #pragma once
@@ -392,15 +395,39 @@ struct MixedBody {
 };
 
 // ---------------------------------------------------------------- producer
+// The CTA's tiles: a contiguous run [begin, end) of the launch's tiles.
+struct TileRange {
+  uint32_t begin, end;
+};
+__device__ __forceinline__ TileRange cta_tiles(uint32_t total_tiles) {
+  const uint32_t per = (total_tiles + gridDim.x - 1) / gridDim.x;
+  const uint32_t b = min(blockIdx.x * per, total_tiles);
+  return TileRange{b, min(b + per, total_tiles)};
+}
+
 template <int W, int LAYOUT>
 __device__ __forceinline__ void producer_loop(const JobParams& p, const StripeDesc* stripes, const uint64_t* ptrs,
                                               const uint32_t* coef, TileHeader* headers, Ring& ring,
                                               uint32_t n_stripes, uint32_t total_tiles) {
   if (p.inject == kInjectProducerStall && blockIdx.x == 0) return;  // test hook, see job.hpp
+  const TileRange tr = cta_tiles(total_tiles);
+  if (tr.begin >= tr.end) return;
   uint32_t q = 0;
   bool ok = true;
-  for (uint32_t tile = blockIdx.x; tile < total_tiles && ok; tile += gridDim.x) {
-    const StripeDesc& d = stripes[find_stripe(stripes, n_stripes, tile)];
+  // current stripe, held in registers; re-read only when a tile crosses into
+  // the next stripe
+  uint32_t si = find_stripe(stripes, n_stripes, tr.begin);
+  StripeDesc d = stripes[si];
+  uint32_t next_begin = si + 1 < n_stripes ? stripes[si + 1].tile_begin : total_tiles;
+  bool fresh = true;      // header fields of this stripe not yet in shared memory
+  uint32_t prev_h = 0;    // slot whose header holds this stripe's fields
+  for (uint32_t tile = tr.begin; tile < tr.end && ok; ++tile) {
+    while (tile >= next_begin) {
+      ++si;
+      d = stripes[si];
+      next_begin = si + 1 < n_stripes ? stripes[si + 1].tile_begin : total_tiles;
+      fresh = true;
+    }
     const TileGeom g = tile_geom(d, tile - d.tile_begin, ring.slice, W);
     const uint64_t* ip = ptrs + d.ptr_off;
     for (int i = 0; i < d.n_in; ++i) {
@@ -427,11 +454,20 @@ __device__ __forceinline__ void producer_loop(const JobParams& p, const StripeDe
         h.k = d.k;
         h.n_pos = d.n_pos;
         h.e = d.e;
-        for (int t = 0; t < kMaxM; ++t) h.outp[t] = t < (int)d.n_out ? ip[d.n_in + t] : 0ull;
-        if (d.op == kOpDecode || d.op == kOpMatDecode) {
-          const int words = selector_words((int)d.m, W);
-          for (int q = 0; q < words; ++q) h.coef[q] = coef[d.coef_off + q];
+        const bool dec = d.op == kOpDecode || d.op == kOpMatDecode;
+        const int words = dec ? selector_words((int)d.m, W) : 0;
+        if (fresh) {
+          for (int t = 0; t < kMaxM; ++t) h.outp[t] = t < (int)d.n_out ? ip[d.n_in + t] : 0ull;
+          for (int c = 0; c < words; ++c) h.coef[c] = coef[d.coef_off + c];
+          fresh = false;
+        } else if (prev_h != s) {
+          // same stripe: output pointers and coefficients from the previous
+          // tile's header (no other header is written in between)
+          const TileHeader& o = headers[prev_h];
+          for (int t = 0; t < kMaxM; ++t) h.outp[t] = o.outp[t];
+          for (int c = 0; c < words; ++c) h.coef[c] = o.coef[c];
         }
+        prev_h = s;
       }
       uint8_t* dst = ring.slots + (size_t)s * ring.slice;
       const uint8_t* src = reinterpret_cast<const uint8_t*>(ip[i]) + g.goff;
@@ -446,8 +482,12 @@ __device__ __forceinline__ void producer_loop(const JobParams& p, const StripeDe
       } else {
         const uint32_t span = ring.slice / (uint32_t)W;
         mbar_arrive_expect_tx(&ring.full[s], ring.slice);
-        for (int c = 0; c < W; ++c)
-          tma_load_1d(dst + (size_t)c * span, src + (size_t)c * d.packet_bytes + g.span_off, span, &ring.full[s]);
+        if (span == d.packet_bytes) {  // whole packets: the W rows are contiguous
+          tma_load_1d(dst, src, ring.slice, &ring.full[s]);
+        } else {
+          for (int c = 0; c < W; ++c)
+            tma_load_1d(dst + (size_t)c * span, src + (size_t)c * d.packet_bytes + g.span_off, span, &ring.full[s]);
+        }
       }
       ring.advance();
       ++q;
@@ -511,7 +551,8 @@ __global__ void __launch_bounds__((Body::kMaxWarps + 1) * 32, Body::kMinBlocks)
     tile.word = (uint32_t)(warp * 32 + lane);
     tile.span = ring.slice / (uint32_t)W;
   }
-  for (uint32_t t = blockIdx.x; t < total_tiles; t += gridDim.x) {
+  const TileRange tr = cta_tiles(total_tiles);
+  for (uint32_t t = tr.begin; t < tr.end; ++t) {
     // the tile's header is published by its first slot's full barrier
     wait_or_fail(&ring.full[ring.s], ring.par, tile.failed, p.status, kDevErrTimeoutFull, p.wait_limit_ns);
     if (tile.failed) break;
