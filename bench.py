@@ -44,6 +44,43 @@ WORKLOAD = ("RS(10,4) GF(2^8), 1 GiB data in 102 stripes of 10 x 1 MiB blocks; p
             "erasures per stripe (min-read)")
 
 
+# DRAM traffic (dram__bytes_read.sum + dram__bytes_write.sum) per stripe of
+# each bench kernel, from one ncu capture of `python bench.py --profile-case
+# <op>` (16 stripes, one launch) divided by 16; a bench launch streams 102
+# stripes, so its traffic is 102 x this.  Valid only for the kernel sources
+# with the recorded digest (kernel_digest()); otherwise reported as null.
+TRAFFIC = {"digest": "f88e1b84060816ac", "per_stripe": {
+    "poly_encode": 12707728,
+    "poly_decode": 12522704,
+    "vandermonde_encode": 12623760,
+    "vandermonde_decode": 12520480,
+    "cauchy_encode": 12605536,
+    "cauchy_decode": 12875328}}
+
+
+def kernel_digest() -> str:
+    """sha256 over the CUDA/C++ sources and the build script of the library."""
+    import hashlib
+
+    h = hashlib.sha256()
+    pkg = os.path.join(ROOT, "paper_1312_5155_gb300")
+    csrc = os.path.join(pkg, "csrc")
+    for name in sorted(os.listdir(csrc)):
+        if name.endswith((".hpp", ".cuh", ".cu", ".cpp")):
+            with open(os.path.join(csrc, name), "rb") as f:
+                h.update(name.encode() + b"\0" + f.read())
+    with open(os.path.join(pkg, "build.py"), "rb") as f:
+        h.update(f.read())
+    return h.hexdigest()[:16]
+
+
+def traffic_per_launch(op_name: str, stripes: int):
+    per = TRAFFIC["per_stripe"].get(op_name)
+    if per is None or TRAFFIC["digest"] != kernel_digest():
+        return None
+    return int(per * stripes)
+
+
 def peaks():
     path = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(path):
@@ -267,7 +304,9 @@ def run_ours(args, rank, world, device):
         "user_gbs": round(user, 2),
         "ops": ops,
         "roofline": {"bound": "hbm", "kernel": f"{dom[0]}_{dom[1]}", "achieved": dom_gbs, "peak": peak,
-                     "peak_kind": kind, "unit": "GB/s", "frac": round(dom_gbs / peak, 4), "traffic": None},
+                     "peak_kind": kind, "unit": "GB/s", "frac": round(dom_gbs / peak, 4),
+                     "traffic": traffic_per_launch(f"{dom[0]}_{dom[1]}", S),
+                     "algorithmic_bytes": S * op_bytes(dom[1]), "kernel_digest": kernel_digest()},
         "launch_shapes": {k2: {"consumer_warps": v[0], "depth": v[1], "ctas_per_sm": v[2]}
                           for k2, v in wl.shapes.items()},
         "gpu_launches": args.steps * wl.launches(),
@@ -376,16 +415,17 @@ def oracle_sample(seconds_target: float = 12.0):
         return time.perf_counter() - t
 
     t_one = one(0)
-    per_thread = max(1, int(seconds_target / max(t_one, 1e-3) / 2))
-    nstripes = min(cores * per_thread, n_stripes())
+    per_thread = max(1, int(seconds_target / max(t_one, 1e-3)))
+    nstripes = cores * per_thread  # stripe indices taken modulo the workload's stripes
     t0 = time.perf_counter()
     with cf.ThreadPoolExecutor(cores) as ex:
-        list(ex.map(one, range(1, 1 + nstripes)))
+        list(ex.map(one, [s % n_stripes() for s in range(1, 1 + nstripes)]))
     dt = time.perf_counter() - t0
     step_bytes = nstripes * len(REALIZATIONS) * 2 * (K + M) * BLOCK
     return {"value": round(step_bytes / dt / 1e9, 4), "unit": "GB/s", "cores": cores, "kind": "oracle",
-            "sample": f"{nstripes} of the 102 RS(10,4) 1 MiB-block stripes, encode + 4-erasure decode in each of "
-                      f"the 3 realizations, one stripe per thread on {cores} host threads ({dt:.1f} s)"}
+            "sample": f"{nstripes} stripe passes over the 102 RS(10,4) 1 MiB-block stripes, encode + 4-erasure "
+                      f"decode in each of the 3 realizations, one stripe per thread on {cores} host threads "
+                      f"({dt:.1f} s wall)"}
 
 
 def run_reference(args, rank, world):

@@ -251,20 +251,26 @@ class Server:
         slot["reqs"] = reqs
 
 
-def serial_run(requests, payloads, results, codes, device):
-    """Every request alone, in arrival order (copies, one launch, sync)."""
+def serial_run(requests, payloads, results, codes, device, max_wall: float | None = None):
+    """Every request alone, in arrival order (copies, one launch, sync).
+    One device buffer per codeword length, sized for the largest block of
+    the run.  With max_wall, requests not started by then stay incomplete
+    (an overloaded serial path falls behind without bound)."""
     import torch
     t0 = time.perf_counter()
+    cap = max((r.block_bytes for r in requests), default=16)
+    cap = (cap + 15) // 16 * 16
     bufs = {}
     for r in requests:
         now = time.perf_counter() - t0
+        if max_wall is not None and now > max_wall:
+            break
         if r.arrival > now:
             time.sleep(r.arrival - now)
         n, B = r.k + r.m, r.block_bytes
-        key = (n, B)
-        if key not in bufs:
-            bufs[key] = torch.empty((n, (B + 15) // 16 * 16), dtype=torch.uint8, device=device)
-        buf = bufs[key]
+        if n not in bufs:
+            bufs[n] = torch.empty((n, cap), dtype=torch.uint8, device=device)
+        buf = bufs[n]
         blocks = [buf[b, :B] for b in range(n)]
         h2d, d2h = io_blocks(r)
         for b in h2d:
@@ -368,7 +374,7 @@ def main():
             from . import rs
             codes = {c: rs.Code(c[0], c[1], 8, "poly") for c in CODES}
             reqs2 = make_requests(inputs.config_seed(5), rate, a.seconds)
-            serial_run(reqs2, payloads, results, codes, torch.device("cuda"))
+            serial_run(reqs2, payloads, results, codes, torch.device("cuda"), max_wall=2.0 * a.seconds)
             row["serial"] = summarize(reqs2)
         out["runs"].append(row)
         print(json.dumps(row), flush=True)

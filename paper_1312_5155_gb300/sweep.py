@@ -1,0 +1,268 @@
+"""Throughput sweeps over the workload configurations of the polynomial
+realization study (§5: random in-memory data, encode and decode of RS(k, m)
+stripes; §5 Fig. 1-4: block size, k and m sweeps), run through the C ABI on
+one GPU.
+
+    python -m paper_1312_5155_gb300.sweep <name> [...]
+
+Names:
+  config1   RS(10,4) poly, one stripe of 10 x 64 KiB: latency of one
+            rs_encode / rs_decode call, and throughput of 1024 replicated
+            stripes in one batched launch
+  config2   RS(6,3) and RS(10,4), GF(2^8), 1 GiB of data cut into stripes of
+            B = 4 KiB * 2^i (i = 0..14), poly / Vandermonde / Cauchy
+            (P = min(2 KiB, B/8)): batched encode, then batched decode with m
+            seeded erasures per stripe
+  config3   RS(12,4) GF(2^16) little-endian, 42 stripes of 4 MiB blocks:
+            poly and Cauchy encode, decode with e = 1..4
+  config4   4096 stripes, (k, m) uniform over (6,3) (10,4) (12,4) (20,4),
+            B log-uniform on [4 KiB, 8 MiB] (multiples of 4 KiB), 30 %
+            decodes with e uniform in 1..m, poly: one batched launch set vs a
+            loop of per-stripe rs_encode / rs_decode calls
+  kmsweep   (k, 4) for k = 2..20 and (10, m) for m = 2..6, GF(2^8), 1 MiB
+            blocks, 1 GiB of data, all three realizations
+
+Every line printed is one JSON object.  Bytes are algorithmic: encode
+(k + m) B, decode (k + e) B per stripe (min-read); "user_gbs" is k B / t.
+Inputs are the seeded SplitMix64 streams of inputs.py; times are CUDA events
+on the launching stream after warm-up, median of the timed repetitions.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import statistics
+
+from . import autotune, inputs, rs
+
+GIB = 1 << 30
+# launch shapes tried per case (consumer warps, ring depth, CTAs per SM): the
+# ones the bench's autotuner picks for these kernels
+SHAPES = [(16, 8, 1), (16, 12, 1), (8, 12, 2), (8, 8, 2)]
+
+
+def _torch():
+    import torch
+    if not torch.cuda.is_available():
+        raise SystemExit("a CUDA device is required")
+    return torch
+
+
+def _time(fn, reps=10, warm=3):
+    torch = _torch()
+    for _ in range(warm):
+        fn()
+    torch.cuda.synchronize()
+    ts = []
+    for _ in range(reps):
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record()
+        fn()
+        e1.record()
+        torch.cuda.synchronize()
+        ts.append(e0.elapsed_time(e1))
+    return statistics.median(ts)
+
+
+def _fill(buf, seed, k, B, stripes):
+    """Data blocks of stripes 0..stripes-1 of a config's byte stream."""
+    torch = _torch()
+    per = max(1, (256 << 20) // max(1, k * B))
+    for s0 in range(0, stripes, per):
+        s1 = min(stripes, s0 + per)
+        buf[s0:s1, :k] = inputs.random_bytes_torch(seed, s0 * k * B, (s1 - s0) * k * B, "cuda").view(s1 - s0, k, B)
+    torch.cuda.synchronize()
+
+
+def _packet(real, w, B):
+    if real != "cauchy":
+        return None
+    return min(2048, B // w)
+
+
+def _batch_pair(real, w, k, m, B, stripes, seed, e, tune=True, tag=""):
+    """Time batched encode and decode of `stripes` stripes; returns a dict."""
+    torch = _torch()
+    n = k + m
+    buf = torch.empty((stripes, n, B), dtype=torch.uint8, device="cuda")
+    _fill(buf, seed, k, B, stripes)
+    code = rs.Code(k, m, w, real, packet_bytes=_packet(real, w, B))
+    base = buf.data_ptr()
+    rows = [[base + (s * n + j) * B for j in range(n)] for s in range(stripes)]  # device pointers
+    sms = torch.cuda.get_device_properties(0).multi_processor_count
+    enc_ops = [(code, "encode", [], rows[s], B) for s in range(stripes)]
+    dec_ops = [(code, "decode", inputs.erasure_pattern(seed, s, n, e), rows[s], B) for s in range(stripes)]
+    out = {}
+    for op, ops in (("encode", enc_ops), ("decode", dec_ops)):
+        b = rs.Batch(stripes)
+        b.set(ops)
+        if tune:
+            key = autotune.make_key(f"sweep{tag}{stripes}-{op}", real, k, m, w, B, sms)
+            shape, _ = autotune.tune_batch(b, ops, key=key, candidates=SHAPES)
+        else:
+            shape = (8, 16, 1)
+            b.set_launch(*shape)
+            b.set(ops)
+        ms = _time(b.launch)
+        if b.poll_status() != 0:
+            raise RuntimeError(f"device status set ({real} {op})")
+        nbytes = stripes * ((k + m) if op == "encode" else (k + e)) * B
+        out[op] = {"ms": round(ms, 4), "gbs": round(nbytes / ms / 1e6, 1),
+                   "user_gbs": round(stripes * k * B / ms / 1e6, 1), "shape": list(shape)}
+        b.close()
+    del buf
+    torch.cuda.empty_cache()
+    return out
+
+
+def config1():
+    torch = _torch()
+    k, m, w, B = 10, 4, 8, 64 << 10
+    seed = inputs.config_seed(1)
+    n = k + m
+    buf = torch.empty((n, B), dtype=torch.uint8, device="cuda")
+    _fill(buf.view(1, n, B), seed, k, B, 1)
+    code = rs.Code(k, m, w, "poly")
+    rows = list(buf)
+    er = inputs.erasure_pattern(seed, 0, n, m)
+    lat_e = _time(lambda: code.encode(rows[:k], rows[k:], B), reps=50)
+    lat_d = _time(lambda: code.decode(er, rows, B), reps=50)
+    print(json.dumps({"config": 1, "what": "one stripe, one call", "encode_us": round(lat_e * 1e3, 1),
+                      "decode_us": round(lat_d * 1e3, 1)}), flush=True)
+    del buf
+    r = _batch_pair("poly", w, k, m, B, 1024, seed, m, tag="c1-")
+    print(json.dumps({"config": 1, "what": "1024 replicated stripes, batched", **r}), flush=True)
+
+
+def config2(blocks=None, codes=((6, 3), (10, 4)), reals=("poly", "vandermonde", "cauchy")):
+    seed = inputs.config_seed(2)
+    for (k, m) in codes:
+        for i in (blocks if blocks is not None else range(15)):
+            B = 4096 << i
+            stripes = max(1, GIB // (k * B))
+            for real in reals:
+                r = _batch_pair(real, 8, k, m, B, stripes, seed, m, tag="c2-")
+                print(json.dumps({"config": 2, "k": k, "m": m, "B": B, "stripes": stripes, "realization": real,
+                                  "packet_bytes": _packet(real, 8, B), **r}), flush=True)
+
+
+def config3():
+    torch = _torch()
+    k, m, w, B, stripes = 12, 4, 16, 4 << 20, 42
+    seed = inputs.config_seed(3)
+    n = k + m
+    for real in ("poly", "cauchy"):
+        buf = torch.empty((stripes, n, B), dtype=torch.uint8, device="cuda")
+        _fill(buf, seed, k, B, stripes)
+        code = rs.Code(k, m, w, real, packet_bytes=_packet(real, w, B))
+        rows = [list(buf[s]) for s in range(stripes)]
+        res = {}
+        b = rs.Batch(stripes)
+        b.set([(code, "encode", [], rows[s], B) for s in range(stripes)])
+        ms = _time(b.launch)
+        res["encode"] = {"ms": round(ms, 4), "gbs": round(stripes * n * B / ms / 1e6, 1)}
+        for e in range(1, m + 1):
+            d = rs.Batch(stripes)
+            d.set([(code, "decode", inputs.erasure_pattern(seed, s, n, e), rows[s], B) for s in range(stripes)])
+            ms = _time(d.launch)
+            if d.poll_status() != 0:
+                raise RuntimeError("device status set")
+            res[f"decode_e{e}"] = {"ms": round(ms, 4), "gbs": round(stripes * (k + e) * B / ms / 1e6, 1)}
+            d.close()
+        b.close()
+        print(json.dumps({"config": 3, "realization": real, "w": w, "B": B, "stripes": stripes, **res}), flush=True)
+        del buf
+        torch.cuda.empty_cache()
+
+
+def config4(stripes=4096, reps=5):
+    torch = _torch()
+    seed = inputs.config_seed(4)
+    codes = [(6, 3), (10, 4), (12, 4), (20, 4)]
+    u = inputs.uniform01(inputs.shape_draws(seed, 0, 4 * stripes)).reshape(stripes, 4)
+    shapes = []
+    for s in range(stripes):
+        k, m = codes[int(u[s, 0] * 4) % 4]
+        B = int(math.exp(math.log(4096) + u[s, 1] * (math.log(8 << 20) - math.log(4096)))) // 4096 * 4096
+        B = max(4096, B)
+        dec = u[s, 2] < 0.30
+        e = 1 + int(u[s, 3] * m) % m if dec else 0
+        shapes.append((k, m, B, e))
+    total = sum((k + m) * B for k, m, B, _ in shapes)
+    arena = torch.empty(total, dtype=torch.uint8, device="cuda")
+    code = {c: rs.Code(c[0], c[1], 8, "poly") for c in codes}
+    views, off = [], 0
+    for s, (k, m, B, e) in enumerate(shapes):
+        v = arena[off:off + (k + m) * B].view(k + m, B)
+        v[:k] = inputs.random_bytes_torch(seed, off, k * B, "cuda").view(k, B)
+        views.append(v)
+        off += (k + m) * B
+    torch.cuda.synchronize()
+    # valid parity first so the decodes rebuild real codewords
+    enc_all = rs.Batch(stripes)
+    enc_all.set([(code[(k, m)], "encode", [], list(views[s]), B) for s, (k, m, B, e) in enumerate(shapes)])
+    enc_all.launch()
+    torch.cuda.synchronize()
+    ops = []
+    for s, (k, m, B, e) in enumerate(shapes):
+        if e:
+            ops.append((code[(k, m)], "decode", inputs.erasure_pattern(seed, s, k + m, e), list(views[s]), B))
+        else:
+            ops.append((code[(k, m)], "encode", [], list(views[s]), B))
+    nbytes = sum((k + m) * B if not e else (k + e) * B for k, m, B, e in shapes)
+    b = rs.Batch(stripes)
+    sms = torch.cuda.get_device_properties(0).multi_processor_count
+    autotune.tune_batch(b, ops, key=autotune.make_key(f"config4-{stripes}", "poly-mixed", 0, 0, 8, 1 << 20, sms))
+    ms_batch = _time(b.launch, reps=reps, warm=2)
+    if b.poll_status() != 0:
+        raise RuntimeError("device status set")
+    # the same ops as a loop of per-stripe calls on one stream
+    calls = []
+    for c, op, er, rows, B in ops:
+        if op == "encode":
+            k = c.k
+            calls.append((c.encode, (rows[:k], rows[k:], B)))
+        else:
+            calls.append((c.decode, (er, rows, B)))
+
+    def loop():
+        for f, a in calls:
+            f(*a)
+
+    ms_loop = _time(loop, reps=reps, warm=1)
+    print(json.dumps({"config": 4, "stripes": stripes, "bytes": nbytes, "gib_resident": round(total / GIB, 2),
+                      "decodes": sum(1 for x in shapes if x[3]), "kernel_launches_batched": b.kernel_count,
+                      "batched": {"ms": round(ms_batch, 3), "gbs": round(nbytes / ms_batch / 1e6, 1)},
+                      "per_stripe_loop": {"ms": round(ms_loop, 3), "gbs": round(nbytes / ms_loop / 1e6, 1)}}),
+          flush=True)
+    b.close()
+    enc_all.close()
+
+
+def kmsweep():
+    seed = inputs.config_seed(2)
+    B = 1 << 20
+    for (k, m) in [(k, 4) for k in range(2, 21)] + [(10, m) for m in (2, 3, 5, 6)]:
+        stripes = max(1, GIB // (k * B))
+        for real in ("poly", "vandermonde", "cauchy"):
+            r = _batch_pair(real, 8, k, m, B, stripes, seed, m, tag="km-")
+            print(json.dumps({"sweep": "km", "k": k, "m": m, "B": B, "stripes": stripes, "realization": real,
+                              **r}), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser(description=__doc__, formatter_class=argparse.RawDescriptionHelpFormatter)
+    ap.add_argument("name", nargs="+", choices=["config1", "config2", "config3", "config4", "kmsweep"])
+    ap.add_argument("--blocks", default=None, help="config2: comma-separated exponents i (B = 4 KiB * 2^i)")
+    a = ap.parse_args()
+    for name in a.name:
+        if name == "config2" and a.blocks:
+            config2(blocks=[int(x) for x in a.blocks.split(",")])
+        else:
+            globals()[name]()
+
+
+if __name__ == "__main__":
+    main()
