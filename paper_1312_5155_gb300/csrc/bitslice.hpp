@@ -44,6 +44,17 @@ struct StaticFor<N, N> {
 };
 
 
+// Bit i of x moved to bit 63 - i.
+RS_HD uint64_t bit_reverse64(uint64_t x) {
+#if defined(__CUDA_ARCH__)
+  return __brevll(x);
+#else
+  uint64_t r = 0;
+  for (int i = 0; i < 64; ++i) r |= ((x >> i) & 1ull) << (63 - i);
+  return r;
+#endif
+}
+
 // Shifts by a constant, written as multiplies so that on the GPU they run
 // on the FMA pipe (IMAD / IMAD.HI) and leave the integer-logic pipe, which
 // bounds these kernels, to the XORs.

@@ -213,26 +213,29 @@ struct PolyDecode {
     for (int j = 0; j < M; ++j)
 #pragma unroll
       for (int b = 0; b < W; ++b) S[j][b] = 0;
-    // Horner over positions in groups of W steps (the renaming period);
-    // the count is padded at the top with positions that hold no data,
-    // which leave the zero start value unchanged.
+    // Horner over positions in groups of W steps (the renaming period); the
+    // count is padded at the top with positions that hold no data.  Step i
+    // (from the top) handles position groups*W - 1 - i: bit i of `order` says
+    // whether that position was read.  Until the first read position the
+    // syndromes are zero, so those steps skip their multiply too.
     const int groups = (n_pos + W - 1) / W;
-    int pos = groups * W - 1;
+    const uint64_t order = bit_reverse64(read_mask) >> (64 - groups * W);
+    const uint64_t live = ~((order & (~order + 1ull)) - 1ull);  // steps from the first read one on
     int i = 0;
     for (int g = 0; g < groups; ++g) {
+      const uint32_t ob = (uint32_t)(order >> (g * W));
+      const uint32_t lb = (uint32_t)(live >> (g * W));
       StaticFor<0, W>::run([&](auto St) {
         constexpr int st = decltype(St)::value;
-        const int p = pos - st;
-        if (p < n_pos && ((read_mask >> p) & 1ull)) {
+        if ((ob >> st) & 1u) {
           uint32_t x[W];
           src.load(i++, x);
           transpose<W>(x);
           horner_mul_add<W, M, st>(S, x);
-        } else {
+        } else if ((lb >> st) & 1u) {
           horner_mul<W, M, st>(S);
         }
       });
-      pos -= W;
     }
     apply_and_store<W, M, true>(e, S, sel, dst);
   }

@@ -215,6 +215,13 @@ struct SymTile {
   __device__ __forceinline__ void store(int t, const uint32_t* x) {
     if (failed) return;
     uint8_t* out = reinterpret_cast<uint8_t*>(select_out(outp, t)) + goff;
+    if (whole) {
+#pragma unroll
+      for (int c = 0; c < W / 4; ++c)
+        *reinterpret_cast<uint4*>(out + seg + (uint32_t)c * 512u + lane * 16u) =
+            make_uint4(x[4 * c], x[4 * c + 1], x[4 * c + 2], x[4 * c + 3]);
+      return;
+    }
 #pragma unroll
     for (int c = 0; c < W / 4; ++c) {
       const uint32_t co = seg + (uint32_t)c * 512u + lane * 16u;
