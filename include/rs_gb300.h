@@ -193,6 +193,29 @@ int rs_batch_kernel_count(const rs_batch *batch);
 /* Read and clear the batch's device status word (as rs_poll_status). */
 rs_status rs_batch_poll_status(rs_batch *batch, int *device_status);
 
+/* Batched block transfer.  The paper has no counterpart: moving the blocks
+ * of a batch between host and device with one copy call per block costs a
+ * host-side call per block, which limits a host thread feeding hundreds of
+ * blocks per batch.  Copies range i, bytes[i] bytes from src[i] to dst[i],
+ * for i < n, on `stream`: ranges of at least engine_min_bytes (0 = 4 MiB;
+ * SIZE_MAX = none) as one copy-engine transfer each (no SMs used, but a
+ * set-up cost per transfer), the smaller ones by one gather kernel launch
+ * per 512 of them (no per-range cost, but it occupies SMs while the link
+ * streams).  Every pointer is device memory or page-locked host
+ * memory (cudaHostAlloc / cudaMallocHost / cudaHostRegister; on a system
+ * with unified addressing it is mapped into the device address space and
+ * read or written directly by the kernel at the host link's bandwidth);
+ * pageable memory is rejected.
+ * Pointers 16-byte aligned; any byte count; each range lies inside one
+ * allocation (as for cudaMemcpy).  Ranges must not overlap one another's
+ * destinations.  The caller keeps the memory alive and unchanged
+ * until the stream reaches the copy.  No device memory is allocated (the
+ * kernel's descriptors travel as kernel parameters), so the call can be
+ * captured in a CUDA graph.  Errors: RS_EINVAL (null, misaligned, overlapping within a
+ * range, pageable or unknown memory), RS_ENOMEM, RS_ECUDA. */
+rs_status rs_copy_blocks(void *const *dst, const void *const *src, const size_t *bytes, int n,
+                         size_t engine_min_bytes, void *stream);
+
 /* ------------------------------------------------------------------------
  * Allocation-free batched encode.  The paper has no counterpart: this entry
  * point exists for callers that cannot allocate device memory when they

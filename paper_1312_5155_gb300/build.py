@@ -133,7 +133,7 @@ def generate_units() -> list[str]:
 
 def sources() -> list[str]:
     return [os.path.join(CSRC, "capi.cu"), os.path.join(CSRC, "plan.cpp"),
-            os.path.join(CSRC, "noalloc.cu")] + generate_units()
+            os.path.join(CSRC, "noalloc.cu"), os.path.join(CSRC, "copy.cu")] + generate_units()
 
 
 def _obj(src: str) -> str:

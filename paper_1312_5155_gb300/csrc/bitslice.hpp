@@ -282,6 +282,49 @@ __device__ __forceinline__ void xor_selected_w8(uint32_t sel, uint32_t* y, const
         "r"(p1[0]), "r"(p1[1]), "r"(p1[2]), "r"(p1[3]), "r"(p1[4]), "r"(p1[5]), "r"(p1[6]), "r"(p1[7]),
         "r"(sel));
 }
+// GF(2^16) form: 16 y planes %0-%15 (logical order), S0..S3 %16-%79, sel %80;
+// no pair sums (registers), so three- and four-term cases take two
+// instructions per plane.
+template <int ROT, int NS>
+__device__ __forceinline__ void xor_selected_w16(uint32_t sel, uint32_t* y, const uint32_t (*S)[16]) {
+  const uint32_t* s0 = S[0];
+  const uint32_t* s1 = NS > 1 ? S[1] : S[0];
+  const uint32_t* s2 = NS > 2 ? S[2] : S[0];
+  const uint32_t* s3 = NS > 3 ? S[3] : S[0];
+  asm("{\n\t"
+      "ts: .branchtargets L0, L1, L2, L3, L4, L5, L6, L7, L8, L9, L10, L11, L12, L13, L14, L15;\n\t"
+      "brx.idx.uni %80, ts;\n"
+      "L0: bra.uni END;\n"
+      "L1: xor.b32 %0, %0, %16; xor.b32 %1, %1, %17; xor.b32 %2, %2, %18; xor.b32 %3, %3, %19; xor.b32 %4, %4, %20; xor.b32 %5, %5, %21; xor.b32 %6, %6, %22; xor.b32 %7, %7, %23; xor.b32 %8, %8, %24; xor.b32 %9, %9, %25; xor.b32 %10, %10, %26; xor.b32 %11, %11, %27; xor.b32 %12, %12, %28; xor.b32 %13, %13, %29; xor.b32 %14, %14, %30; xor.b32 %15, %15, %31; bra.uni END;\n"
+      "L2: xor.b32 %0, %0, %32; xor.b32 %1, %1, %33; xor.b32 %2, %2, %34; xor.b32 %3, %3, %35; xor.b32 %4, %4, %36; xor.b32 %5, %5, %37; xor.b32 %6, %6, %38; xor.b32 %7, %7, %39; xor.b32 %8, %8, %40; xor.b32 %9, %9, %41; xor.b32 %10, %10, %42; xor.b32 %11, %11, %43; xor.b32 %12, %12, %44; xor.b32 %13, %13, %45; xor.b32 %14, %14, %46; xor.b32 %15, %15, %47; bra.uni END;\n"
+      "L3: lop3.b32 %0, %0, %16, %32, 0x96; lop3.b32 %1, %1, %17, %33, 0x96; lop3.b32 %2, %2, %18, %34, 0x96; lop3.b32 %3, %3, %19, %35, 0x96; lop3.b32 %4, %4, %20, %36, 0x96; lop3.b32 %5, %5, %21, %37, 0x96; lop3.b32 %6, %6, %22, %38, 0x96; lop3.b32 %7, %7, %23, %39, 0x96; lop3.b32 %8, %8, %24, %40, 0x96; lop3.b32 %9, %9, %25, %41, 0x96; lop3.b32 %10, %10, %26, %42, 0x96; lop3.b32 %11, %11, %27, %43, 0x96; lop3.b32 %12, %12, %28, %44, 0x96; lop3.b32 %13, %13, %29, %45, 0x96; lop3.b32 %14, %14, %30, %46, 0x96; lop3.b32 %15, %15, %31, %47, 0x96; bra.uni END;\n"
+      "L4: xor.b32 %0, %0, %48; xor.b32 %1, %1, %49; xor.b32 %2, %2, %50; xor.b32 %3, %3, %51; xor.b32 %4, %4, %52; xor.b32 %5, %5, %53; xor.b32 %6, %6, %54; xor.b32 %7, %7, %55; xor.b32 %8, %8, %56; xor.b32 %9, %9, %57; xor.b32 %10, %10, %58; xor.b32 %11, %11, %59; xor.b32 %12, %12, %60; xor.b32 %13, %13, %61; xor.b32 %14, %14, %62; xor.b32 %15, %15, %63; bra.uni END;\n"
+      "L5: lop3.b32 %0, %0, %16, %48, 0x96; lop3.b32 %1, %1, %17, %49, 0x96; lop3.b32 %2, %2, %18, %50, 0x96; lop3.b32 %3, %3, %19, %51, 0x96; lop3.b32 %4, %4, %20, %52, 0x96; lop3.b32 %5, %5, %21, %53, 0x96; lop3.b32 %6, %6, %22, %54, 0x96; lop3.b32 %7, %7, %23, %55, 0x96; lop3.b32 %8, %8, %24, %56, 0x96; lop3.b32 %9, %9, %25, %57, 0x96; lop3.b32 %10, %10, %26, %58, 0x96; lop3.b32 %11, %11, %27, %59, 0x96; lop3.b32 %12, %12, %28, %60, 0x96; lop3.b32 %13, %13, %29, %61, 0x96; lop3.b32 %14, %14, %30, %62, 0x96; lop3.b32 %15, %15, %31, %63, 0x96; bra.uni END;\n"
+      "L6: lop3.b32 %0, %0, %32, %48, 0x96; lop3.b32 %1, %1, %33, %49, 0x96; lop3.b32 %2, %2, %34, %50, 0x96; lop3.b32 %3, %3, %35, %51, 0x96; lop3.b32 %4, %4, %36, %52, 0x96; lop3.b32 %5, %5, %37, %53, 0x96; lop3.b32 %6, %6, %38, %54, 0x96; lop3.b32 %7, %7, %39, %55, 0x96; lop3.b32 %8, %8, %40, %56, 0x96; lop3.b32 %9, %9, %41, %57, 0x96; lop3.b32 %10, %10, %42, %58, 0x96; lop3.b32 %11, %11, %43, %59, 0x96; lop3.b32 %12, %12, %44, %60, 0x96; lop3.b32 %13, %13, %45, %61, 0x96; lop3.b32 %14, %14, %46, %62, 0x96; lop3.b32 %15, %15, %47, %63, 0x96; bra.uni END;\n"
+      "L7: lop3.b32 %0, %0, %16, %32, 0x96; xor.b32 %0, %0, %48; lop3.b32 %1, %1, %17, %33, 0x96; xor.b32 %1, %1, %49; lop3.b32 %2, %2, %18, %34, 0x96; xor.b32 %2, %2, %50; lop3.b32 %3, %3, %19, %35, 0x96; xor.b32 %3, %3, %51; lop3.b32 %4, %4, %20, %36, 0x96; xor.b32 %4, %4, %52; lop3.b32 %5, %5, %21, %37, 0x96; xor.b32 %5, %5, %53; lop3.b32 %6, %6, %22, %38, 0x96; xor.b32 %6, %6, %54; lop3.b32 %7, %7, %23, %39, 0x96; xor.b32 %7, %7, %55; lop3.b32 %8, %8, %24, %40, 0x96; xor.b32 %8, %8, %56; lop3.b32 %9, %9, %25, %41, 0x96; xor.b32 %9, %9, %57; lop3.b32 %10, %10, %26, %42, 0x96; xor.b32 %10, %10, %58; lop3.b32 %11, %11, %27, %43, 0x96; xor.b32 %11, %11, %59; lop3.b32 %12, %12, %28, %44, 0x96; xor.b32 %12, %12, %60; lop3.b32 %13, %13, %29, %45, 0x96; xor.b32 %13, %13, %61; lop3.b32 %14, %14, %30, %46, 0x96; xor.b32 %14, %14, %62; lop3.b32 %15, %15, %31, %47, 0x96; xor.b32 %15, %15, %63; bra.uni END;\n"
+      "L8: xor.b32 %0, %0, %64; xor.b32 %1, %1, %65; xor.b32 %2, %2, %66; xor.b32 %3, %3, %67; xor.b32 %4, %4, %68; xor.b32 %5, %5, %69; xor.b32 %6, %6, %70; xor.b32 %7, %7, %71; xor.b32 %8, %8, %72; xor.b32 %9, %9, %73; xor.b32 %10, %10, %74; xor.b32 %11, %11, %75; xor.b32 %12, %12, %76; xor.b32 %13, %13, %77; xor.b32 %14, %14, %78; xor.b32 %15, %15, %79; bra.uni END;\n"
+      "L9: lop3.b32 %0, %0, %16, %64, 0x96; lop3.b32 %1, %1, %17, %65, 0x96; lop3.b32 %2, %2, %18, %66, 0x96; lop3.b32 %3, %3, %19, %67, 0x96; lop3.b32 %4, %4, %20, %68, 0x96; lop3.b32 %5, %5, %21, %69, 0x96; lop3.b32 %6, %6, %22, %70, 0x96; lop3.b32 %7, %7, %23, %71, 0x96; lop3.b32 %8, %8, %24, %72, 0x96; lop3.b32 %9, %9, %25, %73, 0x96; lop3.b32 %10, %10, %26, %74, 0x96; lop3.b32 %11, %11, %27, %75, 0x96; lop3.b32 %12, %12, %28, %76, 0x96; lop3.b32 %13, %13, %29, %77, 0x96; lop3.b32 %14, %14, %30, %78, 0x96; lop3.b32 %15, %15, %31, %79, 0x96; bra.uni END;\n"
+      "L10: lop3.b32 %0, %0, %32, %64, 0x96; lop3.b32 %1, %1, %33, %65, 0x96; lop3.b32 %2, %2, %34, %66, 0x96; lop3.b32 %3, %3, %35, %67, 0x96; lop3.b32 %4, %4, %36, %68, 0x96; lop3.b32 %5, %5, %37, %69, 0x96; lop3.b32 %6, %6, %38, %70, 0x96; lop3.b32 %7, %7, %39, %71, 0x96; lop3.b32 %8, %8, %40, %72, 0x96; lop3.b32 %9, %9, %41, %73, 0x96; lop3.b32 %10, %10, %42, %74, 0x96; lop3.b32 %11, %11, %43, %75, 0x96; lop3.b32 %12, %12, %44, %76, 0x96; lop3.b32 %13, %13, %45, %77, 0x96; lop3.b32 %14, %14, %46, %78, 0x96; lop3.b32 %15, %15, %47, %79, 0x96; bra.uni END;\n"
+      "L11: lop3.b32 %0, %0, %16, %32, 0x96; xor.b32 %0, %0, %64; lop3.b32 %1, %1, %17, %33, 0x96; xor.b32 %1, %1, %65; lop3.b32 %2, %2, %18, %34, 0x96; xor.b32 %2, %2, %66; lop3.b32 %3, %3, %19, %35, 0x96; xor.b32 %3, %3, %67; lop3.b32 %4, %4, %20, %36, 0x96; xor.b32 %4, %4, %68; lop3.b32 %5, %5, %21, %37, 0x96; xor.b32 %5, %5, %69; lop3.b32 %6, %6, %22, %38, 0x96; xor.b32 %6, %6, %70; lop3.b32 %7, %7, %23, %39, 0x96; xor.b32 %7, %7, %71; lop3.b32 %8, %8, %24, %40, 0x96; xor.b32 %8, %8, %72; lop3.b32 %9, %9, %25, %41, 0x96; xor.b32 %9, %9, %73; lop3.b32 %10, %10, %26, %42, 0x96; xor.b32 %10, %10, %74; lop3.b32 %11, %11, %27, %43, 0x96; xor.b32 %11, %11, %75; lop3.b32 %12, %12, %28, %44, 0x96; xor.b32 %12, %12, %76; lop3.b32 %13, %13, %29, %45, 0x96; xor.b32 %13, %13, %77; lop3.b32 %14, %14, %30, %46, 0x96; xor.b32 %14, %14, %78; lop3.b32 %15, %15, %31, %47, 0x96; xor.b32 %15, %15, %79; bra.uni END;\n"
+      "L12: lop3.b32 %0, %0, %48, %64, 0x96; lop3.b32 %1, %1, %49, %65, 0x96; lop3.b32 %2, %2, %50, %66, 0x96; lop3.b32 %3, %3, %51, %67, 0x96; lop3.b32 %4, %4, %52, %68, 0x96; lop3.b32 %5, %5, %53, %69, 0x96; lop3.b32 %6, %6, %54, %70, 0x96; lop3.b32 %7, %7, %55, %71, 0x96; lop3.b32 %8, %8, %56, %72, 0x96; lop3.b32 %9, %9, %57, %73, 0x96; lop3.b32 %10, %10, %58, %74, 0x96; lop3.b32 %11, %11, %59, %75, 0x96; lop3.b32 %12, %12, %60, %76, 0x96; lop3.b32 %13, %13, %61, %77, 0x96; lop3.b32 %14, %14, %62, %78, 0x96; lop3.b32 %15, %15, %63, %79, 0x96; bra.uni END;\n"
+      "L13: lop3.b32 %0, %0, %16, %48, 0x96; xor.b32 %0, %0, %64; lop3.b32 %1, %1, %17, %49, 0x96; xor.b32 %1, %1, %65; lop3.b32 %2, %2, %18, %50, 0x96; xor.b32 %2, %2, %66; lop3.b32 %3, %3, %19, %51, 0x96; xor.b32 %3, %3, %67; lop3.b32 %4, %4, %20, %52, 0x96; xor.b32 %4, %4, %68; lop3.b32 %5, %5, %21, %53, 0x96; xor.b32 %5, %5, %69; lop3.b32 %6, %6, %22, %54, 0x96; xor.b32 %6, %6, %70; lop3.b32 %7, %7, %23, %55, 0x96; xor.b32 %7, %7, %71; lop3.b32 %8, %8, %24, %56, 0x96; xor.b32 %8, %8, %72; lop3.b32 %9, %9, %25, %57, 0x96; xor.b32 %9, %9, %73; lop3.b32 %10, %10, %26, %58, 0x96; xor.b32 %10, %10, %74; lop3.b32 %11, %11, %27, %59, 0x96; xor.b32 %11, %11, %75; lop3.b32 %12, %12, %28, %60, 0x96; xor.b32 %12, %12, %76; lop3.b32 %13, %13, %29, %61, 0x96; xor.b32 %13, %13, %77; lop3.b32 %14, %14, %30, %62, 0x96; xor.b32 %14, %14, %78; lop3.b32 %15, %15, %31, %63, 0x96; xor.b32 %15, %15, %79; bra.uni END;\n"
+      "L14: lop3.b32 %0, %0, %32, %48, 0x96; xor.b32 %0, %0, %64; lop3.b32 %1, %1, %33, %49, 0x96; xor.b32 %1, %1, %65; lop3.b32 %2, %2, %34, %50, 0x96; xor.b32 %2, %2, %66; lop3.b32 %3, %3, %35, %51, 0x96; xor.b32 %3, %3, %67; lop3.b32 %4, %4, %36, %52, 0x96; xor.b32 %4, %4, %68; lop3.b32 %5, %5, %37, %53, 0x96; xor.b32 %5, %5, %69; lop3.b32 %6, %6, %38, %54, 0x96; xor.b32 %6, %6, %70; lop3.b32 %7, %7, %39, %55, 0x96; xor.b32 %7, %7, %71; lop3.b32 %8, %8, %40, %56, 0x96; xor.b32 %8, %8, %72; lop3.b32 %9, %9, %41, %57, 0x96; xor.b32 %9, %9, %73; lop3.b32 %10, %10, %42, %58, 0x96; xor.b32 %10, %10, %74; lop3.b32 %11, %11, %43, %59, 0x96; xor.b32 %11, %11, %75; lop3.b32 %12, %12, %44, %60, 0x96; xor.b32 %12, %12, %76; lop3.b32 %13, %13, %45, %61, 0x96; xor.b32 %13, %13, %77; lop3.b32 %14, %14, %46, %62, 0x96; xor.b32 %14, %14, %78; lop3.b32 %15, %15, %47, %63, 0x96; xor.b32 %15, %15, %79; bra.uni END;\n"
+      "L15: lop3.b32 %0, %0, %16, %32, 0x96; lop3.b32 %0, %0, %48, %64, 0x96; lop3.b32 %1, %1, %17, %33, 0x96; lop3.b32 %1, %1, %49, %65, 0x96; lop3.b32 %2, %2, %18, %34, 0x96; lop3.b32 %2, %2, %50, %66, 0x96; lop3.b32 %3, %3, %19, %35, 0x96; lop3.b32 %3, %3, %51, %67, 0x96; lop3.b32 %4, %4, %20, %36, 0x96; lop3.b32 %4, %4, %52, %68, 0x96; lop3.b32 %5, %5, %21, %37, 0x96; lop3.b32 %5, %5, %53, %69, 0x96; lop3.b32 %6, %6, %22, %38, 0x96; lop3.b32 %6, %6, %54, %70, 0x96; lop3.b32 %7, %7, %23, %39, 0x96; lop3.b32 %7, %7, %55, %71, 0x96; lop3.b32 %8, %8, %24, %40, 0x96; lop3.b32 %8, %8, %56, %72, 0x96; lop3.b32 %9, %9, %25, %41, 0x96; lop3.b32 %9, %9, %57, %73, 0x96; lop3.b32 %10, %10, %26, %42, 0x96; lop3.b32 %10, %10, %58, %74, 0x96; lop3.b32 %11, %11, %27, %43, 0x96; lop3.b32 %11, %11, %59, %75, 0x96; lop3.b32 %12, %12, %28, %44, 0x96; lop3.b32 %12, %12, %60, %76, 0x96; lop3.b32 %13, %13, %29, %45, 0x96; lop3.b32 %13, %13, %61, %77, 0x96; lop3.b32 %14, %14, %30, %46, 0x96; lop3.b32 %14, %14, %62, %78, 0x96; lop3.b32 %15, %15, %31, %47, 0x96; lop3.b32 %15, %15, %63, %79, 0x96;\n"
+      "END:\n\t}"
+      : "+r"(y[rotated(0, ROT, 16)]), "+r"(y[rotated(1, ROT, 16)]), "+r"(y[rotated(2, ROT, 16)]), "+r"(y[rotated(3, ROT, 16)]),
+        "+r"(y[rotated(4, ROT, 16)]), "+r"(y[rotated(5, ROT, 16)]), "+r"(y[rotated(6, ROT, 16)]), "+r"(y[rotated(7, ROT, 16)]),
+        "+r"(y[rotated(8, ROT, 16)]), "+r"(y[rotated(9, ROT, 16)]), "+r"(y[rotated(10, ROT, 16)]), "+r"(y[rotated(11, ROT, 16)]),
+        "+r"(y[rotated(12, ROT, 16)]), "+r"(y[rotated(13, ROT, 16)]), "+r"(y[rotated(14, ROT, 16)]), "+r"(y[rotated(15, ROT, 16)])
+      : "r"(s0[0]), "r"(s0[1]), "r"(s0[2]), "r"(s0[3]), "r"(s0[4]), "r"(s0[5]), "r"(s0[6]), "r"(s0[7]),
+        "r"(s0[8]), "r"(s0[9]), "r"(s0[10]), "r"(s0[11]), "r"(s0[12]), "r"(s0[13]), "r"(s0[14]), "r"(s0[15]),
+        "r"(s1[0]), "r"(s1[1]), "r"(s1[2]), "r"(s1[3]), "r"(s1[4]), "r"(s1[5]), "r"(s1[6]), "r"(s1[7]),
+        "r"(s1[8]), "r"(s1[9]), "r"(s1[10]), "r"(s1[11]), "r"(s1[12]), "r"(s1[13]), "r"(s1[14]), "r"(s1[15]),
+        "r"(s2[0]), "r"(s2[1]), "r"(s2[2]), "r"(s2[3]), "r"(s2[4]), "r"(s2[5]), "r"(s2[6]), "r"(s2[7]),
+        "r"(s2[8]), "r"(s2[9]), "r"(s2[10]), "r"(s2[11]), "r"(s2[12]), "r"(s2[13]), "r"(s2[14]), "r"(s2[15]),
+        "r"(s3[0]), "r"(s3[1]), "r"(s3[2]), "r"(s3[3]), "r"(s3[4]), "r"(s3[5]), "r"(s3[6]), "r"(s3[7]),
+        "r"(s3[8]), "r"(s3[9]), "r"(s3[10]), "r"(s3[11]), "r"(s3[12]), "r"(s3[13]), "r"(s3[14]), "r"(s3[15]),
+        "r"(sel));
+}
 #endif
 
 // y ^= the subset of S[0..NS-1] named by the 4-bit selector sel.
@@ -290,6 +333,9 @@ RS_HD void xor_selected(uint32_t sel, uint32_t* y, const uint32_t (*S)[W], const
 #if defined(__CUDA_ARCH__)
   if constexpr (W == 8) {
     xor_selected_w8<ROT, NS>(sel, y, S, P);
+    return;
+  } else if constexpr (W == 16) {
+    xor_selected_w16<ROT, NS>(sel, y, S);
     return;
   }
 #endif

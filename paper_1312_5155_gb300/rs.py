@@ -71,6 +71,9 @@ def lib() -> ctypes.CDLL:
                                                                    ctypes.c_int, ctypes.POINTER(VP),
                                                                    ctypes.POINTER(VP),
                                                                    ctypes.POINTER(ctypes.c_size_t), VP]),
+                "rs_copy_blocks": (ctypes.c_int, [ctypes.POINTER(VP), ctypes.POINTER(VP),
+                                                   ctypes.POINTER(ctypes.c_size_t), ctypes.c_int,
+                                                   ctypes.c_size_t, VP]),
                 "rs_batch_create": (ctypes.c_int, [ctypes.c_int, ctypes.POINTER(VP)]),
                 "rs_batch_destroy": (None, [VP]),
                 "rs_batch_set_launch": (ctypes.c_int, [VP, ctypes.c_int, ctypes.c_int, ctypes.c_int]),
@@ -313,6 +316,24 @@ class Batch:
             self.close()
         except Exception:
             pass
+
+
+# ------------------------------------------------- batched block transfer
+ENGINE_NEVER = (1 << 64) - 1
+
+
+def rs_copy_blocks(dst, src, nbytes, stream=None, engine_min_bytes: int = 0) -> None:
+    """Copy range i (nbytes[i] bytes) from src[i] to dst[i] for every i:
+    ranges of at least engine_min_bytes (0 = 4 MiB, ENGINE_NEVER = none) on
+    the copy engines, the others by one gather kernel launch per 512.  Each
+    pointer (int or tensor) is device memory or page-locked host memory;
+    16-byte aligned."""
+    n = len(nbytes)
+    if len(dst) != n or len(src) != n:
+        raise ValueError("dst, src and nbytes need one entry per range")
+    bb = (ctypes.c_size_t * max(1, n))(*nbytes)
+    _check(lib().rs_copy_blocks(_ptr_array(list(dst)), _ptr_array(list(src)), bb, n, engine_min_bytes,
+                                _stream(stream)))
 
 
 # ------------------------------------------------- allocation-free encode

@@ -8,8 +8,9 @@ arrive over time.  The loop:
   - as soon as one of `streams` launch slots is free, packs every admitted
     request into one batch (rs_batch_set + rs_batch_launch: one persistent
     launch per kernel group) on that slot's stream, preceded by the
-    host->device copy of the request's input blocks and followed by the
-    device->host copy of its output blocks;
+    host->device transfer of the requests' input blocks and followed by the
+    device->host transfer of their output blocks (rs_copy_blocks: one launch
+    per direction for the whole batch);
   - polls the slots' completion events; a finished request frees its arena
     memory, which admits the next arrivals.
 Requests arriving while earlier batches run are admitted and launched on
@@ -216,39 +217,55 @@ class Server:
         return requests
 
     def _launch(self, slot, reqs, payloads, results):
-        """One batch on the slot's stream: inputs in (one copy of the k data
-        rows for an encode, of the whole stripe for a decode), one launch per
-        kernel group, outputs out (the m parity rows in one copy; the erased
-        rows of a decode one by one).  Block pointers are computed from the
-        arena base, so no tensor views are made per block."""
-        torch = self.torch
+        """One batch on the slot's stream: the input blocks of every request
+        in (encode: the k data rows; decode: the k rows a min-read decode
+        reads), one launch per kernel group, the output blocks out (parity
+        rows; rebuilt rows).  Both transfers are one rs_copy_blocks call each,
+        all ranges on the gather kernel (one launch reading / writing the
+        page-locked host buffers: no per-range set-up cost), with the ranges
+        of consecutive rows of a request merged.  Block pointers are
+        computed from the arena base, so no tensor views are made per block."""
+        torch, rs = self.torch, self.rs
         st = slot["stream"]
         ops = []
+        src, dst, nb = [], [], []
+        for r in reqs:
+            n, B = r.k + r.m, r.block_bytes
+            Bp = (B + 15) // 16 * 16
+            base = self.base + r.off
+            hp = payloads[r.rid].data_ptr()
+            for i, b in enumerate(io_blocks(r)[0]):
+                _add_range(dst, src, nb, base + b * Bp, hp + b * B, B, join=i > 0)
+            ops.append((self.codes[(r.k, r.m)], r.op, r.erasures, [base + b * Bp for b in range(n)], B))
         with torch.cuda.stream(st):
-            for r in reqs:
-                n, B = r.k + r.m, r.block_bytes
-                Bp = (B + 15) // 16 * 16
-                base = self.base + r.off
-                stripe = self.mem[r.off:r.off + n * Bp].view(n, Bp)
-                if r.op == "encode":
-                    stripe[:r.k, :B].copy_(payloads[r.rid][:r.k], non_blocking=True)
-                else:
-                    stripe[:, :B].copy_(payloads[r.rid], non_blocking=True)
-                ops.append((self.codes[(r.k, r.m)], r.op, r.erasures, [base + b * Bp for b in range(n)], B))
+            rs.rs_copy_blocks(dst, src, nb, stream=st, engine_min_bytes=rs.ENGINE_NEVER)
             slot["batch"].set(ops, stream=st)
             slot["batch"].launch(stream=st)
             if results is not None:
+                src, dst, nb = [], [], []
                 for r in reqs:
-                    n, B = r.k + r.m, r.block_bytes
+                    B = r.block_bytes
                     Bp = (B + 15) // 16 * 16
-                    stripe = self.mem[r.off:r.off + n * Bp].view(n, Bp)
-                    if r.op == "encode":
-                        results[r.rid].copy_(stripe[r.k:, :B], non_blocking=True)
-                    else:
-                        for j, b in enumerate(r.erasures):
-                            results[r.rid][j].copy_(stripe[b, :B], non_blocking=True)
+                    base = self.base + r.off
+                    res = results[r.rid].data_ptr()
+                    for j, b in enumerate(io_blocks(r)[1]):
+                        _add_range(dst, src, nb, res + j * B, base + b * Bp, B, join=j > 0)
+                rs.rs_copy_blocks(dst, src, nb, stream=st, engine_min_bytes=rs.ENGINE_NEVER)
             slot["event"].record(st)
         slot["reqs"] = reqs
+
+
+def _add_range(dst, src, nb, d, s, n, join=True):
+    """Append a copy range, extending the previous one when `join` (the two
+    belong to the same host buffer) and both ends follow on from it.  Ranges
+    of different host buffers stay apart even when adjacent in memory: a
+    copy-engine transfer must not cross from one allocation into another."""
+    if join and nb and dst[-1] + nb[-1] == d and src[-1] + nb[-1] == s:
+        nb[-1] += n
+    else:
+        dst.append(d)
+        src.append(s)
+        nb.append(n)
 
 
 def serial_run(requests, payloads, results, codes, device, max_wall: float | None = None):

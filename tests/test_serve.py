@@ -88,3 +88,14 @@ def test_served_results_equal_alone_results_and_oracle():
         assert np.array_equal(alone[r.rid].numpy(), results[r.rid].numpy()), r.rid
     for s in srv.slots:
         assert s["batch"].poll_status() == 0
+
+
+def test_add_range_merges_consecutive_rows():
+    from paper_1312_5155_gb300.serve import _add_range
+    d, s, n = [], [], []
+    _add_range(d, s, n, 1000, 5000, 16)
+    _add_range(d, s, n, 1016, 5016, 32)   # follows on: merged
+    _add_range(d, s, n, 2000, 5048, 16)   # destination jumps: new range
+    _add_range(d, s, n, 2016, 9000, 16)   # source jumps: new range
+    _add_range(d, s, n, 2032, 9016, 16, join=False)  # another buffer: kept apart
+    assert (d, s, n) == ([1000, 2000, 2016, 2032], [5000, 5048, 9000, 9016], [48, 16, 16, 16])
