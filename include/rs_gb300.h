@@ -110,6 +110,25 @@ rs_status rs_set_launch(rs_code *code, int consumer_warps, int depth, int ctas_p
 rs_status rs_encode(rs_code *code, const void *const *data_ptrs, void *const *parity_ptrs,
                     size_t block_bytes, void *stream);
 
+/* Delta update of one stripe's parity after data block `index` changed.
+ * §3.2's update remark: the code is linear, so the encode of the data
+ * diff-blocks is the parity diff; with only block `index` changed by
+ * delta = new XOR old, parity block j changes by P[j][index] * delta, where
+ * P[:, index] is the encode of the unit data vector (x^(m+index) mod g(x)
+ * for the polynomial code, the generator's parity column for the matrix
+ * realizations).  Every realization and layout: delta and the parity
+ * blocks are in the code's layout (packets for the bit-matrix
+ * realizations).
+ *   index: data block in [0, k);
+ *   delta: device pointer to block_bytes bytes (read only);
+ *   parity_ptrs: host array of m device pointers, updated in place
+ *   (parity_j ^= P[j][index] * delta);
+ *   block_bytes as for rs_encode.
+ * Errors: RS_EINVAL (index, null, misalignment, overlap, size),
+ * RS_EUNSUPPORTED, RS_ECUDA. */
+rs_status rs_update(rs_code *code, int index, const void *delta, void *const *parity_ptrs, size_t block_bytes,
+                    void *stream);
+
 /* Decode one stripe: rebuild the erased blocks.  §3.3 (polynomial: Step 1
  * evaluates D(alpha^j) over the read survivors, Step 2 solves the small
  * Vandermonde system, inverted once per erasure pattern on the host), §2.1

@@ -69,6 +69,7 @@ struct rs_code {
   TuneCfg tune;
   std::vector<uint32_t> P;       // parity rows of the generator (matrix realizations)
   uint32_t* d_pmask = nullptr;   // column masks of P on the device (runtime-P kernels)
+  uint32_t* d_update = nullptr;  // per data index i: columns [P[:, i] | I_m] as bits (rs_update)
   bool fixed = false;            // compile-time-P kernels exist for (w, k, m)
   int device = 0;
   int num_sms = 0;
@@ -205,6 +206,45 @@ rs_status prepare_encode(rs_code* c, const void* const* data, void* const* parit
   } else {
     for (int i = 0; i < c->k; ++i) po.ptrs.push_back((uint64_t)(uintptr_t)data[i]);
   }
+  for (int j = 0; j < c->m; ++j) po.ptrs.push_back((uint64_t)(uintptr_t)parity[j]);
+  po.coef.clear();
+  return RS_OK;
+}
+
+// Delta update (§3.2's update remark: the encode of the data diff-blocks is
+// the parity diff): data block `index` changed by delta, so parity block j
+// gains P[j][index] * delta.  Run as the runtime-matrix encode of the m + 1
+// inputs (delta, p_0 .. p_(m-1)) by U = [P[:, index] | I_m], the outputs
+// written over p_0 .. p_(m-1): every tile reads its slice of a block before
+// it writes the same slice, and no other tile touches those bytes.
+rs_status prepare_update(rs_code* c, int index, const void* delta, void* const* parity, size_t B, PreparedOp& po) {
+  if (index < 0 || index >= c->k) return fail(RS_EINVAL, "data index out of range");
+  if (!parity) return fail(RS_EINVAL, "pointer array is null");
+  std::vector<const void*> all{delta};
+  for (int j = 0; j < c->m; ++j) all.push_back(parity[j]);
+  rs_status s = check_blocks(c, all, B);
+  if (s != RS_OK) return s;
+  KernelKey key;
+  key.family = kFamMatRuntime;
+  key.w = c->w;
+  key.m = c->m;
+  key.op = kOpMatEncode;
+  key.layout = packet_layout(c->real) ? kLayoutPacket : kLayoutSymbol;
+  po.key = key;
+  po.entry = find_kernel(key);
+  if (!po.entry) return fail(RS_EUNSUPPORTED, "no kernel compiled for this code");
+  po.noop = B == 0;
+  StripeDesc& d = po.d;
+  fill_common(c, B, d);
+  d.k = (uint8_t)(c->m + 1);
+  d.pmask = (uint64_t)(uintptr_t)(c->d_update + (size_t)index * (c->m + 1) * column_words(c->m, c->w));
+  d.n_in = (uint16_t)(c->m + 1);
+  d.n_out = (uint16_t)c->m;
+  d.op = (uint8_t)kOpMatEncode;
+  d.m = (uint8_t)c->m;
+  po.ptrs.clear();
+  po.ptrs.push_back((uint64_t)(uintptr_t)delta);
+  for (int j = 0; j < c->m; ++j) po.ptrs.push_back((uint64_t)(uintptr_t)parity[j]);
   for (int j = 0; j < c->m; ++j) po.ptrs.push_back((uint64_t)(uintptr_t)parity[j]);
   po.coef.clear();
   return RS_OK;
@@ -390,7 +430,9 @@ rs_status rs_init(int k, int m, int w, int realization, rs_code** out) {
     }
   } else if (c->real == Realization::Cauchy) {
     cauchy_parity_matrix(k, m, w, c->P);
-  } else if (c->real != Realization::Poly) {
+  } else {
+    // polynomial code (any of its three realizations): column i of P is
+    // x^(m+i) mod g(x), the parity of the unit data vector e_i
     poly_parity_matrix(k, m, w, c->P);
   }
   c->fixed = c->real != Realization::Poly && has_fixed_kernels(w, k, m, kKindOf[(int)c->real]);
@@ -405,9 +447,26 @@ rs_status rs_init(int k, int m, int w, int realization, rs_code** out) {
     if (e == cudaSuccess)
       e = cudaMemcpy(c->d_pmask, masks.data(), masks.size() * sizeof(uint32_t), cudaMemcpyHostToDevice);
   }
+  if (e == cudaSuccess) {
+    // update matrices U_i = [P[:, i] | I_m] (m x (m + 1)), one after another
+    std::vector<uint32_t> all;
+    std::vector<uint32_t> U((size_t)m * (m + 1));
+    for (int i = 0; i < k; ++i) {
+      for (int j = 0; j < m; ++j) {
+        U[(size_t)j * (m + 1)] = c->P[(size_t)j * k + i];
+        for (int l = 0; l < m; ++l) U[(size_t)j * (m + 1) + 1 + l] = j == l ? 1u : 0u;
+      }
+      const std::vector<uint32_t> cols = pack_columns(U, m + 1, m, w);
+      all.insert(all.end(), cols.begin(), cols.end());
+    }
+    e = cudaMalloc(&c->d_update, all.size() * sizeof(uint32_t));
+    if (e == cudaSuccess)
+      e = cudaMemcpy(c->d_update, all.data(), all.size() * sizeof(uint32_t), cudaMemcpyHostToDevice);
+  }
   if (e != cudaSuccess) {
     if (c->d_status) cudaFree(c->d_status);
     if (c->d_pmask) cudaFree(c->d_pmask);
+    if (c->d_update) cudaFree(c->d_update);
     delete c;
     return cuda_fail(e, "rs_init");
   }
@@ -419,6 +478,7 @@ void rs_destroy(rs_code* c) {
   if (!c) return;
   if (c->d_status) cudaFree(c->d_status);
   if (c->d_pmask) cudaFree(c->d_pmask);
+  if (c->d_update) cudaFree(c->d_update);
   delete c;
 }
 
@@ -467,6 +527,15 @@ rs_status rs_decode(rs_code* c, const int* erasures, int n_erasures, void* const
   if (!c) return fail(RS_EINVAL, "code is null");
   PreparedOp po;
   rs_status s = prepare_decode(c, erasures, n_erasures, block_ptrs, block_bytes, po);
+  if (s != RS_OK) return s;
+  return launch_single(c, po, stream);
+}
+
+rs_status rs_update(rs_code* c, int index, const void* delta, void* const* parity_ptrs, size_t block_bytes,
+                    void* stream) {
+  if (!c) return fail(RS_EINVAL, "code is null");
+  PreparedOp po;
+  rs_status s = prepare_update(c, index, delta, parity_ptrs, block_bytes, po);
   if (s != RS_OK) return s;
   return launch_single(c, po, stream);
 }

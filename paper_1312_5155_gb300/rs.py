@@ -64,6 +64,7 @@ def lib() -> ctypes.CDLL:
                 "rs_encode": (ctypes.c_int, [VP, ctypes.POINTER(VP), ctypes.POINTER(VP), ctypes.c_size_t, VP]),
                 "rs_decode": (ctypes.c_int, [VP, ctypes.POINTER(ctypes.c_int), ctypes.c_int,
                                              ctypes.POINTER(VP), ctypes.c_size_t, VP]),
+                "rs_update": (ctypes.c_int, [VP, ctypes.c_int, VP, ctypes.POINTER(VP), ctypes.c_size_t, VP]),
                 "rs_poll_status": (ctypes.c_int, [VP, ctypes.POINTER(ctypes.c_int)]),
                 "rs_set_wait_limit": (ctypes.c_int, [VP, ctypes.c_ulonglong]),
                 "rs_inject_fault": (ctypes.c_int, [VP, ctypes.c_int]),
@@ -205,6 +206,14 @@ class Code:
         if block_bytes is None:
             block_bytes = int(blocks[0].numel() * blocks[0].element_size())
         rs_decode(self.handle, list(erasures), list(blocks), block_bytes, stream)
+
+    def update(self, index: int, delta, parity, block_bytes: int | None = None, stream=None):
+        """Parity after data block `index` changed by `delta` (new XOR old):
+        parity_j ^= P[j][index] * delta, in place (§3.2's update remark)."""
+        if block_bytes is None:
+            block_bytes = int(delta.numel() * delta.element_size())
+        _check(lib().rs_update(self.handle, index, _ptr(delta), _ptr_array(list(parity)), block_bytes,
+                               _stream(stream)))
 
     def poll_status(self) -> int:
         return rs_poll_status(self.handle)
