@@ -100,7 +100,9 @@ def _batch_pair(real, w, k, m, B, stripes, seed, e, tune=True, tag=""):
         b.set(ops)
         if tune:
             key = autotune.make_key(f"sweep{tag}{stripes}-{op}", real, k, m, w, B, sms)
-            shape, _ = autotune.tune_batch(b, ops, key=key, candidates=SHAPES)
+            # small blocks fill only narrow tiles: try the tuner's whole list
+            shape, _ = autotune.tune_batch(b, ops, key=key,
+                                           candidates=autotune.CANDIDATES if B <= (16 << 10) else SHAPES)
         else:
             shape = (8, 16, 1)
             b.set_launch(*shape)
