@@ -21,6 +21,9 @@ Names:
             loop of per-stripe rs_encode / rs_decode calls
   kmsweep   (k, 4) for k = 2..20 and (10, m) for m = 2..6, GF(2^8), 1 MiB
             blocks, 1 GiB of data, all three realizations
+  polyforms the polynomial code as LFSR, through its generator matrix and
+            through that matrix's bit-matrix (packets), RS(10,4), RS(12,4),
+            RS(6,3), 1 MiB blocks
 
 Every line printed is one JSON object.  Bytes are algorithmic: encode
 (k + m) B, decode (k + e) B per stripe (min-read); "user_gbs" is k B / t.
@@ -77,7 +80,7 @@ def _fill(buf, seed, k, B, stripes):
 
 
 def _packet(real, w, B):
-    if real != "cauchy":
+    if real not in ("cauchy", "poly_bitmatrix"):
         return None
     return min(2048, B // w)
 
@@ -254,9 +257,24 @@ def kmsweep():
                               **r}), flush=True)
 
 
+def polyforms():
+    """The three device forms of the polynomial code (§3 LFSR; §6's open
+    questions: its generator matrix in the symbol layout and that matrix's
+    bit-matrix projection over packets), RS(10,4) and RS(12,4) over 1 GiB
+    of 1 MiB blocks."""
+    seed = inputs.config_seed(2)
+    B = 1 << 20
+    for (k, m) in ((10, 4), (12, 4), (6, 3)):
+        stripes = max(1, GIB // (k * B))
+        for real in ("poly", "poly_matrix", "poly_bitmatrix"):
+            r = _batch_pair(real, 8, k, m, B, stripes, seed, m, tag="pf-")
+            print(json.dumps({"sweep": "polyforms", "k": k, "m": m, "B": B, "stripes": stripes,
+                              "realization": real, **r}), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser(description=__doc__, formatter_class=argparse.RawDescriptionHelpFormatter)
-    ap.add_argument("name", nargs="+", choices=["config1", "config2", "config3", "config4", "kmsweep"])
+    ap.add_argument("name", nargs="+", choices=["config1", "config2", "config3", "config4", "kmsweep", "polyforms"])
     ap.add_argument("--blocks", default=None, help="config2: comma-separated exponents i (B = 4 KiB * 2^i)")
     a = ap.parse_args()
     for name in a.name:
