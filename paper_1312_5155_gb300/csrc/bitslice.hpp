@@ -200,6 +200,13 @@ struct Selectors {
 #pragma unroll
     for (int i = 0; i < kWords; ++i) w[i] = src.word(i);
   }
+  // Nibble n of a row (runtime n; selects instead of indexing).
+  static RS_HD uint32_t nibble(const uint32_t* r, int n) {
+    uint32_t v = r[0];
+#pragma unroll
+    for (int q = 1; q < kRowWords; ++q) v = ((n >> 3) == q) ? r[q] : v;
+    return (v >> ((n & 7) * 4)) & 15u;
+  }
   // Words of row t (runtime t; selects instead of indexing so that w stays
   // in registers).
   RS_HD void row(int t, uint32_t* r) const {
