@@ -288,7 +288,8 @@ int rso_poly_decode_column(int w, int k, int m, const int *er, int e,
     if (check_erasures(n, m, er, e)) return -1;
     if (e == 0) return 0;
     uint32_t D[256], V[256 * 256];
-    if (e > 256) return -1;
+    if (e < 0 || e > 256) return -1;
+    const size_t ue = (size_t)e;
     char erased[512];
     if (n > 512) return -1;
     memset(erased, 0, sizeof(erased));
@@ -303,8 +304,8 @@ int rso_poly_decode_column(int w, int k, int m, const int *er, int e,
         for (int t = 0; t < e; t++)
             V[j * e + t] = gpow_alpha(f, (uint64_t)j * (uint64_t)poly_pos(k, m, er[t]));
     }
-    if (D_out) memcpy(D_out, D, sizeof(uint32_t) * (size_t)e);
-    if (V_out) memcpy(V_out, V, sizeof(uint32_t) * (size_t)e * e);
+    if (D_out) memcpy(D_out, D, sizeof(uint32_t) * ue);
+    if (V_out) memcpy(V_out, V, sizeof(uint32_t) * ue * ue);
     int rc = gauss_solve(f, e, V, D);
     if (rc) return rc;
     for (int t = 0; t < e; t++) c[er[t]] = D[t];
