@@ -49,8 +49,9 @@ def instances():
     for w in (8, 16):
         for m in M_RANGE[w]:
             for op in (0, 1):
-                out.append((f"poly_w{w}_m{m}_op{op}", f"PolyBody<{w}, {m}, {op}>",
-                            dict(family=0, w=w, m=m, op=op)))
+                # GF(2^8) decodes with M <= 4: two column groups per lane
+                body = f"PolyDecode2Body<{w}, {m}>" if (op == 1 and w == 8 and m <= 4) else f"PolyBody<{w}, {m}, {op}>"
+                out.append((f"poly_w{w}_m{m}_op{op}", body, dict(family=0, w=w, m=m, op=op)))
     for w in (8, 16):
         for m in M_RANGE[w]:
             for op in (2, 3):
@@ -107,19 +108,21 @@ def generate_units() -> list[str]:
             f"cudaError_t launch_{name}(const JobParams& p, const LaunchShape& sh, cudaStream_t st) {{\n"
             f"  return launch_body<{body}>(p, sh, st);\n}}\n"
             f"int warps_{name}() {{ return {body}::kMaxWarps; }}\n"
+            f"int groups_{name}() {{ return {body}::kGroups; }}\n"
             "}  // namespace rsgb\n"))
         units.append(path)
     lines = ["// generated by paper_1312_5155_gb300/build.py", '#include "registry.hpp"', "namespace rsgb {"]
     for name, _, _ in insts:
         lines.append(f"cudaError_t launch_{name}(const JobParams&, const LaunchShape&, cudaStream_t);")
         lines.append(f"int warps_{name}();")
+        lines.append(f"int groups_{name}();")
     lines.append("static const KernelEntry* build_table() {")
     lines.append(f"  static KernelEntry t[{len(insts)}];")
     for i, (name, _, key) in enumerate(insts):
         k = dict(family=0, w=0, m=0, op=0, layout=0, kind=0, k=0, mset=0)
         k.update(key)
         lines.append(f"  t[{i}] = KernelEntry{{KernelKey{{{k['family']}, {k['w']}, {k['m']}, {k['op']}, "
-                     f"{k['layout']}, {k['kind']}, {k['k']}, {k['mset']}u}}, launch_{name}, warps_{name}(), "
+                     f"{k['layout']}, {k['kind']}, {k['k']}, {k['mset']}u}}, launch_{name}, warps_{name}(), groups_{name}(), "
                      f'"{name}"}};')
     lines.append("  return t;\n}")
     lines.append("const KernelEntry* const kKernelRegistryPtr = build_table();")

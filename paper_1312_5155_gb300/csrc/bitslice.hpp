@@ -334,6 +334,79 @@ __device__ __forceinline__ void xor_selected_w16(uint32_t sel, uint32_t* y, cons
 }
 #endif
 
+#if defined(__CUDA_ARCH__)
+// Two 32-column groups at once (GF(2^8), no pair sums): y0 %0-%7 and y1
+// %8-%15 (logical planes), the four syndromes of group 0 %16-%47 and of
+// group 1 %48-%79, sel %80.  Operands of syndromes beyond NS feed only
+// unreachable cases and are bound to syndrome 0.
+template <int ROT, int NS>
+__device__ __forceinline__ void xor_selected2_w8(uint32_t sel, uint32_t* y0, uint32_t* y1, const uint32_t (*A)[8],
+                                                 const uint32_t (*B)[8]) {
+  const uint32_t *a0 = A[0], *a1 = NS > 1 ? A[1] : A[0], *a2 = NS > 2 ? A[2] : A[0], *a3 = NS > 3 ? A[3] : A[0];
+  const uint32_t *b0 = B[0], *b1 = NS > 1 ? B[1] : B[0], *b2 = NS > 2 ? B[2] : B[0], *b3 = NS > 3 ? B[3] : B[0];
+  asm("{\n\t"
+      "ts: .branchtargets L0, L1, L2, L3, L4, L5, L6, L7, L8, L9, L10, L11, L12, L13, L14, L15;\n\t"
+      "brx.idx.uni %80, ts;\n"
+      "L0: bra.uni END;\n"
+      "L1: xor.b32 %0, %0, %16; xor.b32 %1, %1, %17; xor.b32 %2, %2, %18; xor.b32 %3, %3, %19; xor.b32 %4, %4, %20; xor.b32 %5, %5, %21; xor.b32 %6, %6, %22; xor.b32 %7, %7, %23; xor.b32 %8, %8, %48; xor.b32 %9, %9, %49; xor.b32 %10, %10, %50; xor.b32 %11, %11, %51; xor.b32 %12, %12, %52; xor.b32 %13, %13, %53; xor.b32 %14, %14, %54; xor.b32 %15, %15, %55; bra.uni END;\n"
+      "L2: xor.b32 %0, %0, %24; xor.b32 %1, %1, %25; xor.b32 %2, %2, %26; xor.b32 %3, %3, %27; xor.b32 %4, %4, %28; xor.b32 %5, %5, %29; xor.b32 %6, %6, %30; xor.b32 %7, %7, %31; xor.b32 %8, %8, %56; xor.b32 %9, %9, %57; xor.b32 %10, %10, %58; xor.b32 %11, %11, %59; xor.b32 %12, %12, %60; xor.b32 %13, %13, %61; xor.b32 %14, %14, %62; xor.b32 %15, %15, %63; bra.uni END;\n"
+      "L3: lop3.b32 %0, %0, %16, %24, 0x96; lop3.b32 %1, %1, %17, %25, 0x96; lop3.b32 %2, %2, %18, %26, 0x96; lop3.b32 %3, %3, %19, %27, 0x96; lop3.b32 %4, %4, %20, %28, 0x96; lop3.b32 %5, %5, %21, %29, 0x96; lop3.b32 %6, %6, %22, %30, 0x96; lop3.b32 %7, %7, %23, %31, 0x96; lop3.b32 %8, %8, %48, %56, 0x96; lop3.b32 %9, %9, %49, %57, 0x96; lop3.b32 %10, %10, %50, %58, 0x96; lop3.b32 %11, %11, %51, %59, 0x96; lop3.b32 %12, %12, %52, %60, 0x96; lop3.b32 %13, %13, %53, %61, 0x96; lop3.b32 %14, %14, %54, %62, 0x96; lop3.b32 %15, %15, %55, %63, 0x96; bra.uni END;\n"
+      "L4: xor.b32 %0, %0, %32; xor.b32 %1, %1, %33; xor.b32 %2, %2, %34; xor.b32 %3, %3, %35; xor.b32 %4, %4, %36; xor.b32 %5, %5, %37; xor.b32 %6, %6, %38; xor.b32 %7, %7, %39; xor.b32 %8, %8, %64; xor.b32 %9, %9, %65; xor.b32 %10, %10, %66; xor.b32 %11, %11, %67; xor.b32 %12, %12, %68; xor.b32 %13, %13, %69; xor.b32 %14, %14, %70; xor.b32 %15, %15, %71; bra.uni END;\n"
+      "L5: lop3.b32 %0, %0, %16, %32, 0x96; lop3.b32 %1, %1, %17, %33, 0x96; lop3.b32 %2, %2, %18, %34, 0x96; lop3.b32 %3, %3, %19, %35, 0x96; lop3.b32 %4, %4, %20, %36, 0x96; lop3.b32 %5, %5, %21, %37, 0x96; lop3.b32 %6, %6, %22, %38, 0x96; lop3.b32 %7, %7, %23, %39, 0x96; lop3.b32 %8, %8, %48, %64, 0x96; lop3.b32 %9, %9, %49, %65, 0x96; lop3.b32 %10, %10, %50, %66, 0x96; lop3.b32 %11, %11, %51, %67, 0x96; lop3.b32 %12, %12, %52, %68, 0x96; lop3.b32 %13, %13, %53, %69, 0x96; lop3.b32 %14, %14, %54, %70, 0x96; lop3.b32 %15, %15, %55, %71, 0x96; bra.uni END;\n"
+      "L6: lop3.b32 %0, %0, %24, %32, 0x96; lop3.b32 %1, %1, %25, %33, 0x96; lop3.b32 %2, %2, %26, %34, 0x96; lop3.b32 %3, %3, %27, %35, 0x96; lop3.b32 %4, %4, %28, %36, 0x96; lop3.b32 %5, %5, %29, %37, 0x96; lop3.b32 %6, %6, %30, %38, 0x96; lop3.b32 %7, %7, %31, %39, 0x96; lop3.b32 %8, %8, %56, %64, 0x96; lop3.b32 %9, %9, %57, %65, 0x96; lop3.b32 %10, %10, %58, %66, 0x96; lop3.b32 %11, %11, %59, %67, 0x96; lop3.b32 %12, %12, %60, %68, 0x96; lop3.b32 %13, %13, %61, %69, 0x96; lop3.b32 %14, %14, %62, %70, 0x96; lop3.b32 %15, %15, %63, %71, 0x96; bra.uni END;\n"
+      "L7: lop3.b32 %0, %0, %16, %24, 0x96; xor.b32 %0, %0, %32; lop3.b32 %1, %1, %17, %25, 0x96; xor.b32 %1, %1, %33; lop3.b32 %2, %2, %18, %26, 0x96; xor.b32 %2, %2, %34; lop3.b32 %3, %3, %19, %27, 0x96; xor.b32 %3, %3, %35; lop3.b32 %4, %4, %20, %28, 0x96; xor.b32 %4, %4, %36; lop3.b32 %5, %5, %21, %29, 0x96; xor.b32 %5, %5, %37; lop3.b32 %6, %6, %22, %30, 0x96; xor.b32 %6, %6, %38; lop3.b32 %7, %7, %23, %31, 0x96; xor.b32 %7, %7, %39; lop3.b32 %8, %8, %48, %56, 0x96; xor.b32 %8, %8, %64; lop3.b32 %9, %9, %49, %57, 0x96; xor.b32 %9, %9, %65; lop3.b32 %10, %10, %50, %58, 0x96; xor.b32 %10, %10, %66; lop3.b32 %11, %11, %51, %59, 0x96; xor.b32 %11, %11, %67; lop3.b32 %12, %12, %52, %60, 0x96; xor.b32 %12, %12, %68; lop3.b32 %13, %13, %53, %61, 0x96; xor.b32 %13, %13, %69; lop3.b32 %14, %14, %54, %62, 0x96; xor.b32 %14, %14, %70; lop3.b32 %15, %15, %55, %63, 0x96; xor.b32 %15, %15, %71; bra.uni END;\n"
+      "L8: xor.b32 %0, %0, %40; xor.b32 %1, %1, %41; xor.b32 %2, %2, %42; xor.b32 %3, %3, %43; xor.b32 %4, %4, %44; xor.b32 %5, %5, %45; xor.b32 %6, %6, %46; xor.b32 %7, %7, %47; xor.b32 %8, %8, %72; xor.b32 %9, %9, %73; xor.b32 %10, %10, %74; xor.b32 %11, %11, %75; xor.b32 %12, %12, %76; xor.b32 %13, %13, %77; xor.b32 %14, %14, %78; xor.b32 %15, %15, %79; bra.uni END;\n"
+      "L9: lop3.b32 %0, %0, %16, %40, 0x96; lop3.b32 %1, %1, %17, %41, 0x96; lop3.b32 %2, %2, %18, %42, 0x96; lop3.b32 %3, %3, %19, %43, 0x96; lop3.b32 %4, %4, %20, %44, 0x96; lop3.b32 %5, %5, %21, %45, 0x96; lop3.b32 %6, %6, %22, %46, 0x96; lop3.b32 %7, %7, %23, %47, 0x96; lop3.b32 %8, %8, %48, %72, 0x96; lop3.b32 %9, %9, %49, %73, 0x96; lop3.b32 %10, %10, %50, %74, 0x96; lop3.b32 %11, %11, %51, %75, 0x96; lop3.b32 %12, %12, %52, %76, 0x96; lop3.b32 %13, %13, %53, %77, 0x96; lop3.b32 %14, %14, %54, %78, 0x96; lop3.b32 %15, %15, %55, %79, 0x96; bra.uni END;\n"
+      "L10: lop3.b32 %0, %0, %24, %40, 0x96; lop3.b32 %1, %1, %25, %41, 0x96; lop3.b32 %2, %2, %26, %42, 0x96; lop3.b32 %3, %3, %27, %43, 0x96; lop3.b32 %4, %4, %28, %44, 0x96; lop3.b32 %5, %5, %29, %45, 0x96; lop3.b32 %6, %6, %30, %46, 0x96; lop3.b32 %7, %7, %31, %47, 0x96; lop3.b32 %8, %8, %56, %72, 0x96; lop3.b32 %9, %9, %57, %73, 0x96; lop3.b32 %10, %10, %58, %74, 0x96; lop3.b32 %11, %11, %59, %75, 0x96; lop3.b32 %12, %12, %60, %76, 0x96; lop3.b32 %13, %13, %61, %77, 0x96; lop3.b32 %14, %14, %62, %78, 0x96; lop3.b32 %15, %15, %63, %79, 0x96; bra.uni END;\n"
+      "L11: lop3.b32 %0, %0, %16, %24, 0x96; xor.b32 %0, %0, %40; lop3.b32 %1, %1, %17, %25, 0x96; xor.b32 %1, %1, %41; lop3.b32 %2, %2, %18, %26, 0x96; xor.b32 %2, %2, %42; lop3.b32 %3, %3, %19, %27, 0x96; xor.b32 %3, %3, %43; lop3.b32 %4, %4, %20, %28, 0x96; xor.b32 %4, %4, %44; lop3.b32 %5, %5, %21, %29, 0x96; xor.b32 %5, %5, %45; lop3.b32 %6, %6, %22, %30, 0x96; xor.b32 %6, %6, %46; lop3.b32 %7, %7, %23, %31, 0x96; xor.b32 %7, %7, %47; lop3.b32 %8, %8, %48, %56, 0x96; xor.b32 %8, %8, %72; lop3.b32 %9, %9, %49, %57, 0x96; xor.b32 %9, %9, %73; lop3.b32 %10, %10, %50, %58, 0x96; xor.b32 %10, %10, %74; lop3.b32 %11, %11, %51, %59, 0x96; xor.b32 %11, %11, %75; lop3.b32 %12, %12, %52, %60, 0x96; xor.b32 %12, %12, %76; lop3.b32 %13, %13, %53, %61, 0x96; xor.b32 %13, %13, %77; lop3.b32 %14, %14, %54, %62, 0x96; xor.b32 %14, %14, %78; lop3.b32 %15, %15, %55, %63, 0x96; xor.b32 %15, %15, %79; bra.uni END;\n"
+      "L12: lop3.b32 %0, %0, %32, %40, 0x96; lop3.b32 %1, %1, %33, %41, 0x96; lop3.b32 %2, %2, %34, %42, 0x96; lop3.b32 %3, %3, %35, %43, 0x96; lop3.b32 %4, %4, %36, %44, 0x96; lop3.b32 %5, %5, %37, %45, 0x96; lop3.b32 %6, %6, %38, %46, 0x96; lop3.b32 %7, %7, %39, %47, 0x96; lop3.b32 %8, %8, %64, %72, 0x96; lop3.b32 %9, %9, %65, %73, 0x96; lop3.b32 %10, %10, %66, %74, 0x96; lop3.b32 %11, %11, %67, %75, 0x96; lop3.b32 %12, %12, %68, %76, 0x96; lop3.b32 %13, %13, %69, %77, 0x96; lop3.b32 %14, %14, %70, %78, 0x96; lop3.b32 %15, %15, %71, %79, 0x96; bra.uni END;\n"
+      "L13: lop3.b32 %0, %0, %16, %32, 0x96; xor.b32 %0, %0, %40; lop3.b32 %1, %1, %17, %33, 0x96; xor.b32 %1, %1, %41; lop3.b32 %2, %2, %18, %34, 0x96; xor.b32 %2, %2, %42; lop3.b32 %3, %3, %19, %35, 0x96; xor.b32 %3, %3, %43; lop3.b32 %4, %4, %20, %36, 0x96; xor.b32 %4, %4, %44; lop3.b32 %5, %5, %21, %37, 0x96; xor.b32 %5, %5, %45; lop3.b32 %6, %6, %22, %38, 0x96; xor.b32 %6, %6, %46; lop3.b32 %7, %7, %23, %39, 0x96; xor.b32 %7, %7, %47; lop3.b32 %8, %8, %48, %64, 0x96; xor.b32 %8, %8, %72; lop3.b32 %9, %9, %49, %65, 0x96; xor.b32 %9, %9, %73; lop3.b32 %10, %10, %50, %66, 0x96; xor.b32 %10, %10, %74; lop3.b32 %11, %11, %51, %67, 0x96; xor.b32 %11, %11, %75; lop3.b32 %12, %12, %52, %68, 0x96; xor.b32 %12, %12, %76; lop3.b32 %13, %13, %53, %69, 0x96; xor.b32 %13, %13, %77; lop3.b32 %14, %14, %54, %70, 0x96; xor.b32 %14, %14, %78; lop3.b32 %15, %15, %55, %71, 0x96; xor.b32 %15, %15, %79; bra.uni END;\n"
+      "L14: lop3.b32 %0, %0, %24, %32, 0x96; xor.b32 %0, %0, %40; lop3.b32 %1, %1, %25, %33, 0x96; xor.b32 %1, %1, %41; lop3.b32 %2, %2, %26, %34, 0x96; xor.b32 %2, %2, %42; lop3.b32 %3, %3, %27, %35, 0x96; xor.b32 %3, %3, %43; lop3.b32 %4, %4, %28, %36, 0x96; xor.b32 %4, %4, %44; lop3.b32 %5, %5, %29, %37, 0x96; xor.b32 %5, %5, %45; lop3.b32 %6, %6, %30, %38, 0x96; xor.b32 %6, %6, %46; lop3.b32 %7, %7, %31, %39, 0x96; xor.b32 %7, %7, %47; lop3.b32 %8, %8, %56, %64, 0x96; xor.b32 %8, %8, %72; lop3.b32 %9, %9, %57, %65, 0x96; xor.b32 %9, %9, %73; lop3.b32 %10, %10, %58, %66, 0x96; xor.b32 %10, %10, %74; lop3.b32 %11, %11, %59, %67, 0x96; xor.b32 %11, %11, %75; lop3.b32 %12, %12, %60, %68, 0x96; xor.b32 %12, %12, %76; lop3.b32 %13, %13, %61, %69, 0x96; xor.b32 %13, %13, %77; lop3.b32 %14, %14, %62, %70, 0x96; xor.b32 %14, %14, %78; lop3.b32 %15, %15, %63, %71, 0x96; xor.b32 %15, %15, %79; bra.uni END;\n"
+      "L15: lop3.b32 %0, %0, %16, %24, 0x96; lop3.b32 %0, %0, %32, %40, 0x96; lop3.b32 %1, %1, %17, %25, 0x96; lop3.b32 %1, %1, %33, %41, 0x96; lop3.b32 %2, %2, %18, %26, 0x96; lop3.b32 %2, %2, %34, %42, 0x96; lop3.b32 %3, %3, %19, %27, 0x96; lop3.b32 %3, %3, %35, %43, 0x96; lop3.b32 %4, %4, %20, %28, 0x96; lop3.b32 %4, %4, %36, %44, 0x96; lop3.b32 %5, %5, %21, %29, 0x96; lop3.b32 %5, %5, %37, %45, 0x96; lop3.b32 %6, %6, %22, %30, 0x96; lop3.b32 %6, %6, %38, %46, 0x96; lop3.b32 %7, %7, %23, %31, 0x96; lop3.b32 %7, %7, %39, %47, 0x96; lop3.b32 %8, %8, %48, %56, 0x96; lop3.b32 %8, %8, %64, %72, 0x96; lop3.b32 %9, %9, %49, %57, 0x96; lop3.b32 %9, %9, %65, %73, 0x96; lop3.b32 %10, %10, %50, %58, 0x96; lop3.b32 %10, %10, %66, %74, 0x96; lop3.b32 %11, %11, %51, %59, 0x96; lop3.b32 %11, %11, %67, %75, 0x96; lop3.b32 %12, %12, %52, %60, 0x96; lop3.b32 %12, %12, %68, %76, 0x96; lop3.b32 %13, %13, %53, %61, 0x96; lop3.b32 %13, %13, %69, %77, 0x96; lop3.b32 %14, %14, %54, %62, 0x96; lop3.b32 %14, %14, %70, %78, 0x96; lop3.b32 %15, %15, %55, %63, 0x96; lop3.b32 %15, %15, %71, %79, 0x96;\n"
+      "END:\n\t}"
+      : "+r"(y0[rotated(0, ROT, 8)]), "+r"(y0[rotated(1, ROT, 8)]), "+r"(y0[rotated(2, ROT, 8)]), "+r"(y0[rotated(3, ROT, 8)]), "+r"(y0[rotated(4, ROT, 8)]), "+r"(y0[rotated(5, ROT, 8)]), "+r"(y0[rotated(6, ROT, 8)]), "+r"(y0[rotated(7, ROT, 8)]),
+        "+r"(y1[rotated(0, ROT, 8)]), "+r"(y1[rotated(1, ROT, 8)]), "+r"(y1[rotated(2, ROT, 8)]), "+r"(y1[rotated(3, ROT, 8)]), "+r"(y1[rotated(4, ROT, 8)]), "+r"(y1[rotated(5, ROT, 8)]), "+r"(y1[rotated(6, ROT, 8)]), "+r"(y1[rotated(7, ROT, 8)])
+      : "r"(a0[0]), "r"(a0[1]), "r"(a0[2]), "r"(a0[3]), "r"(a0[4]), "r"(a0[5]), "r"(a0[6]), "r"(a0[7]),
+        "r"(a1[0]), "r"(a1[1]), "r"(a1[2]), "r"(a1[3]), "r"(a1[4]), "r"(a1[5]), "r"(a1[6]), "r"(a1[7]),
+        "r"(a2[0]), "r"(a2[1]), "r"(a2[2]), "r"(a2[3]), "r"(a2[4]), "r"(a2[5]), "r"(a2[6]), "r"(a2[7]),
+        "r"(a3[0]), "r"(a3[1]), "r"(a3[2]), "r"(a3[3]), "r"(a3[4]), "r"(a3[5]), "r"(a3[6]), "r"(a3[7]),
+        "r"(b0[0]), "r"(b0[1]), "r"(b0[2]), "r"(b0[3]), "r"(b0[4]), "r"(b0[5]), "r"(b0[6]), "r"(b0[7]),
+        "r"(b1[0]), "r"(b1[1]), "r"(b1[2]), "r"(b1[3]), "r"(b1[4]), "r"(b1[5]), "r"(b1[6]), "r"(b1[7]),
+        "r"(b2[0]), "r"(b2[1]), "r"(b2[2]), "r"(b2[3]), "r"(b2[4]), "r"(b2[5]), "r"(b2[6]), "r"(b2[7]),
+        "r"(b3[0]), "r"(b3[1]), "r"(b3[2]), "r"(b3[3]), "r"(b3[4]), "r"(b3[5]), "r"(b3[6]), "r"(b3[7]),
+        "r"(sel));
+}
+#endif
+
+// y0 ^= subset of A, y1 ^= the same subset of B (two column groups), with
+// y0 and y1 in rotation ROT; the subset is the 4-bit selector sel.
+template <int W, int ROT, int NS>
+RS_HD void xor_selected2(uint32_t sel, uint32_t* y0, uint32_t* y1, const uint32_t (*A)[W], const uint32_t (*B)[W]) {
+#if defined(__CUDA_ARCH__)
+  constexpr bool kTable = W == 8;
+#else
+  constexpr bool kTable = false;
+#endif
+  if constexpr (kTable) {
+#if defined(__CUDA_ARCH__)
+    xor_selected2_w8<ROT, NS>(sel, y0, y1, A, B);
+#endif
+  } else {
+#pragma unroll
+    for (int b = 0; b < W; ++b) {
+      uint32_t z0 = 0, z1 = 0;
+#pragma unroll
+      for (int i = 0; i < NS; ++i)
+        if ((sel >> i) & 1u) {
+          z0 ^= A[i][b];
+          z1 ^= B[i][b];
+        }
+      y0[((b - ROT) % W + W) % W] ^= z0;
+      y1[((b - ROT) % W + W) % W] ^= z1;
+    }
+  }
+}
+
 // y ^= the subset of S[0..NS-1] named by the 4-bit selector sel.
 template <int W, int ROT, int NS>
 RS_HD void xor_selected(uint32_t sel, uint32_t* y, const uint32_t (*S)[W], const uint32_t (*P)[W]) {

@@ -292,8 +292,8 @@ int pick_warps(const TuneCfg& t, int cap, int layout, uint32_t packet_gcd) {
   return nc;
 }
 
-LaunchShape make_shape(const TuneCfg& t, int nc, int w, int num_sms, uint32_t& slice, uint32_t& depth) {
-  slice = (uint32_t)nc * segment_bytes(w);
+LaunchShape make_shape(const TuneCfg& t, int nc, int w, int groups, int num_sms, uint32_t& slice, uint32_t& depth) {
+  slice = (uint32_t)(nc * groups) * segment_bytes(w);
   depth = (uint32_t)std::max(2, t.depth);
   const size_t budget = kMaxDynamicSmem / (size_t)std::max(1, t.ctas_per_sm);
   while (depth > 2 && ring_smem_bytes(depth, slice) > budget) --depth;
@@ -316,7 +316,7 @@ rs_status launch_single(rs_code* c, PreparedOp& po, void* stream) {
   if (!p) return fail(RS_ENOMEM, "host allocation failed");
   const int nc = pick_warps(c->tune, po.entry->max_warps, po.key.layout, po.d.packet_bytes);
   uint32_t slice, depth;
-  LaunchShape sh = make_shape(c->tune, nc, c->w, c->num_sms, slice, depth);
+  LaunchShape sh = make_shape(c->tune, nc, c->w, po.entry->groups, c->num_sms, slice, depth);
   p->status = c->d_status;
   p->n_stripes = 1;
   p->slice_bytes = slice;
@@ -685,7 +685,7 @@ rs_status rs_batch_set(rs_batch* b, const rs_op* ops, int n_ops, void* stream) {
     gr.layout = layout;
     gr.nc = pick_warps(b->tune, gr.entry->max_warps, layout, pg);
     const int w = gr.entry->key.w;
-    gr.sh = make_shape(b->tune, gr.nc, w, b->num_sms, gr.slice, gr.depth);
+    gr.sh = make_shape(b->tune, gr.nc, w, gr.entry->groups, b->num_sms, gr.slice, gr.depth);
     uint32_t tiles = 0;
     StripeDesc* region = hs + g * (size_t)b->max_ops;
     for (size_t q = 0; q < members[g].size(); ++q) {

@@ -26,7 +26,7 @@ namespace rsgb {
 // over groups of M steps needs no register moves.
 template <int W, int M>
 struct PolyEncode {
-  static constexpr int phys(int j, int S) { return ((j - S) % M + M) % M; }
+  static RS_CHD constexpr int phys(int j, int S) { return ((j - S) % M + M) % M; }
 
   template <int S>
   static RS_HD void step(uint32_t (*r)[W], const uint32_t* x) {
@@ -272,6 +272,104 @@ struct PolyDecode {
       }
     }
     apply_and_store<W, M, true>(e, S, sel, dst);
+  }
+};
+
+// Two 32-column groups per thread (G = 2): the same decode as PolyDecode on
+// 2W words (group 0 = words 0..W-1, group 1 = W..2W-1 of every input and
+// output).  Every warp-uniform decision -- the Horner presence test, the
+// barrier waits, the selector dispatch -- then serves 64 columns, and the
+// two groups' instruction streams are independent.  Without pair sums (they
+// would not fit the registers); M <= 4.
+template <int W, int M>
+struct PolyDecode2 {
+  static_assert(M <= 4, "one selector chunk");
+  template <class Src, class Dst, class Coef>
+  static RS_HD void run(int n_pos, uint64_t read_mask, int e, Src& src, Dst& dst, Coef& coef) {
+    Selectors<W, M> sel;
+    sel.load(coef);
+    uint32_t A[M][W], B[M][W];
+#pragma unroll
+    for (int j = 0; j < M; ++j)
+#pragma unroll
+      for (int b = 0; b < W; ++b) A[j][b] = B[j][b] = 0;
+    constexpr int U = kHornerSteps<W>;
+    const int groups = (n_pos + U - 1) / U;
+    const uint64_t order = bit_reverse64(read_mask) >> (64 - groups * U);
+    const uint64_t live = ~((order & (~order + 1ull)) - 1ull);
+    int i = 0;
+#pragma unroll 1
+    for (int g = 0; g < groups; ++g) {
+      const uint32_t ob = (uint32_t)(order >> (g * U));
+      const uint32_t lb = (uint32_t)(live >> (g * U));
+      StaticFor<0, U>::run([&](auto St) {
+        constexpr int st = decltype(St)::value;
+        if ((ob >> st) & 1u) {
+          uint32_t x[2 * W];
+          src.load(i++, x);
+          transpose<W>(x);
+          transpose<W>(x + W);
+          horner_mul_add<W, M, st>(A, x);
+          horner_mul_add<W, M, st>(B, x + W);
+        } else if ((lb >> st) & 1u) {
+          horner_mul<W, M, st>(A);
+          horner_mul<W, M, st>(B);
+        }
+      });
+      if constexpr (U % W != 0) {
+        StaticFor<1, M>::run([&](auto J) {
+          constexpr int j = decltype(J)::value;
+          constexpr int rot = (j * U) % W;
+          if constexpr (rot != 0) {
+            uint32_t ra[W], rb[W];
+#pragma unroll
+            for (int b = 0; b < W; ++b) {
+              ra[b] = A[j][((b - rot) % W + W) % W];
+              rb[b] = B[j][((b - rot) % W + W) % W];
+            }
+#pragma unroll
+            for (int b = 0; b < W; ++b) {
+              A[j][b] = ra[b];
+              B[j][b] = rb[b];
+            }
+          }
+        });
+      }
+    }
+    // erased outputs, one at a time (as apply_and_store, both groups)
+    using Sel = Selectors<W, M>;
+#pragma unroll 1
+    for (int t = 0; t < e; ++t) {
+      uint32_t row[Sel::kRowWords];
+      sel.row(t, row);
+      uint32_t y[2 * W];
+#pragma unroll
+      for (int b = 0; b < 2 * W; ++b) y[b] = 0;
+      constexpr int kSteps = kApplySteps<W>;
+#pragma unroll 1
+      for (int c0 = W - 1; c0 >= 0; c0 -= kSteps) {
+        StaticFor<0, kSteps>::run([&](auto Uu) {
+          constexpr int u = decltype(Uu)::value;
+          const int c = c0 - u;
+          mul_alpha_renamed<W, u>(y);
+          mul_alpha_renamed<W, u>(y + W);
+          xor_selected2<W, u + 1, M>(Sel::nibble(row, c), y, y + W, A, B);
+        });
+        if constexpr (kSteps % W != 0) {
+          uint32_t r[2 * W];
+#pragma unroll
+          for (int b = 0; b < W; ++b) {
+            r[b] = y[((b - kSteps) % W + W) % W];
+            r[W + b] = y[W + ((b - kSteps) % W + W) % W];
+          }
+#pragma unroll
+          for (int b = 0; b < 2 * W; ++b) y[b] = r[b];
+        }
+      }
+      transpose<W>(y);
+      transpose<W>(y + W);
+      dst.store(t, y);
+    }
   }
 };
 

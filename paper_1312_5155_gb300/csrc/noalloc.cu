@@ -126,7 +126,7 @@ extern "C" rs_status rs_poly_encode_stripes_noalloc(int k, int m, int w, int n_s
 
   TuneCfg tune;
   const int nc = std::max(1, std::min(tune.consumer_warps, entry->max_warps));
-  const uint32_t slice = (uint32_t)nc * segment_bytes(w);
+  const uint32_t slice = (uint32_t)(nc * entry->groups) * segment_bytes(w);
   uint32_t depth = (uint32_t)tune.depth;
   while (depth > 2 && ring_smem_bytes(depth, slice) > kMaxDynamicSmem) --depth;
 

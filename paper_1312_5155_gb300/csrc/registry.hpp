@@ -34,6 +34,7 @@ struct KernelEntry {
   KernelKey key;
   Launcher launch;
   int max_warps;
+  int groups;  // 32-column groups per consumer lane (tile slice = warps * groups * segment)
   const char* name;
 };
 

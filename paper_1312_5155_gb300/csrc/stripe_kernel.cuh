@@ -148,7 +148,10 @@ __device__ __forceinline__ uint64_t select_out(const uint64_t (&outp)[MO], int t
 }
 
 // ------------------------------------------------------ consumer tile views
-template <int W, int MO>
+// G column groups per lane: lane l owns the 16-byte chunks at
+// l*16 + c*512 (c < G*W/4) of its warp's segment (G * segment_bytes(W)
+// bytes); group g is words g*W .. g*W+W-1 of a load or store.
+template <int W, int MO, int G = 1>
 struct SymTile {
   Ring* ring;
   const uint64_t* ptrs;  // stripe pointers: inputs then outputs
@@ -169,7 +172,7 @@ struct SymTile {
     goff = h.goff;
     len = h.len;
     // every chunk of this thread lies in the bulk-copied part of the slot
-    whole = seg + (uint32_t)(W / 4 - 1) * 512u + lane * 16u + 16u <= (len & ~15u);
+    whole = seg + (uint32_t)(G * W / 4 - 1) * 512u + lane * 16u + 16u <= (len & ~15u);
 #pragma unroll
     for (int t = 0; t < MO; ++t) outp[t] = h.outp[t];
   }
@@ -185,7 +188,7 @@ struct SymTile {
     const uint8_t* slot = r.slots + (size_t)s * r.slice;
     if (whole) {
 #pragma unroll
-      for (int c = 0; c < W / 4; ++c) {
+      for (int c = 0; c < G * W / 4; ++c) {
         const uint4 v = *reinterpret_cast<const uint4*>(slot + seg + (uint32_t)c * 512u + lane * 16u);
         x[4 * c + 0] = v.x;
         x[4 * c + 1] = v.y;
@@ -195,7 +198,7 @@ struct SymTile {
     } else {
       const uint32_t len16 = len & ~15u;
 #pragma unroll
-      for (int c = 0; c < W / 4; ++c) {
+      for (int c = 0; c < G * W / 4; ++c) {
         const uint32_t co = seg + (uint32_t)c * 512u + lane * 16u;
         uint4 v = make_uint4(0, 0, 0, 0);
         if (co + 16u <= len16) {
@@ -217,13 +220,13 @@ struct SymTile {
     uint8_t* out = reinterpret_cast<uint8_t*>(select_out(outp, t)) + goff;
     if (whole) {
 #pragma unroll
-      for (int c = 0; c < W / 4; ++c)
+      for (int c = 0; c < G * W / 4; ++c)
         *reinterpret_cast<uint4*>(out + seg + (uint32_t)c * 512u + lane * 16u) =
             make_uint4(x[4 * c], x[4 * c + 1], x[4 * c + 2], x[4 * c + 3]);
       return;
     }
 #pragma unroll
-    for (int c = 0; c < W / 4; ++c) {
+    for (int c = 0; c < G * W / 4; ++c) {
       const uint32_t co = seg + (uint32_t)c * 512u + lane * 16u;
       const uint4 v = make_uint4(x[4 * c], x[4 * c + 1], x[4 * c + 2], x[4 * c + 3]);
       if (co + 16u <= len) {
@@ -311,6 +314,7 @@ RS_CHD constexpr int body_min_blocks(int w, int max_warps, int live_words) {
 template <int W, int M, int OP>
 struct PolyBody {
   static constexpr int kW = W;
+  static constexpr int kGroups = 1;
   static constexpr int kLayout = kLayoutSymbol;
   static constexpr int kMaxOut = M;
   static constexpr int kMaxWarps = OP == kOpEncode ? body_warps(M * W) : 8;
@@ -327,9 +331,30 @@ struct PolyBody {
   }
 };
 
+// GF(2^8) polynomial decode with two 32-column groups per lane
+// (PolyDecode2): 64 columns per thread share every warp-uniform decision.
+template <int W, int M>
+struct PolyDecode2Body {
+  static constexpr int kW = W;
+  static constexpr int kGroups = 2;
+  static constexpr int kLayout = kLayoutSymbol;
+  static constexpr int kMaxOut = M;
+  // two groups of syndromes and outputs live at once: 12 consumer warps in
+  // one CTA per SM keep them in registers (128 a thread)
+  static constexpr int kMaxWarps = 12;
+  static constexpr int kMinBlocks = 1;
+  __device__ static bool matches(const TileOp& o) { return o.op == kOpDecode && o.m == M; }
+  template <class Tile>
+  __device__ static void run(const TileOp& o, Tile& t, const uint32_t* coef) {
+    CoefWords cm{coef};
+    PolyDecode2<W, M>::run(o.n_pos, o.read_mask, o.e, t, t, cm);
+  }
+};
+
 template <int W, int M, int OP, int LAYOUT>
 struct MatRuntimeBody {
   static constexpr int kW = W;
+  static constexpr int kGroups = 1;
   static constexpr int kLayout = LAYOUT;
   static constexpr int kMaxOut = M;
   static constexpr int kMaxWarps = OP == kOpMatEncode ? body_warps(M * W + 16) : 8;
@@ -350,6 +375,7 @@ struct MatRuntimeBody {
 template <int W, int K, int M, int KIND, int OP>
 struct MatFixedBody {
   static constexpr int kW = W;
+  static constexpr int kGroups = 1;
   static constexpr int kLayout = kind_layout(KIND);
   static constexpr int kMaxOut = M;
   static constexpr int kMaxWarps = OP == kOpMatEncode ? body_warps(M * W) : 8;
@@ -371,6 +397,8 @@ struct MatFixedBody {
 template <class First, class... Rest>
 struct MixedBody {
   static constexpr int kW = First::kW;
+  static constexpr int kGroups = First::kGroups;
+  static_assert(((Rest::kGroups == First::kGroups) && ...), "one tile geometry per kernel");
   static constexpr int kLayout = First::kLayout;
   static constexpr int min_warps() {
     int w = First::kMaxWarps;
@@ -544,7 +572,8 @@ __global__ void __launch_bounds__((Body::kMaxWarps + 1) * 32, Body::kMinBlocks)
     return;
   }
 
-  using Tile = std::conditional_t<Body::kLayout == kLayoutSymbol, SymTile<W, Body::kMaxOut>,
+  static_assert(Body::kLayout == kLayoutSymbol || Body::kGroups == 1, "packet tiles have one group");
+  using Tile = std::conditional_t<Body::kLayout == kLayoutSymbol, SymTile<W, Body::kMaxOut, Body::kGroups>,
                                   PacketTile<W, Body::kMaxOut>>;
   Tile tile;
   tile.ring = &ring;
@@ -553,7 +582,7 @@ __global__ void __launch_bounds__((Body::kMaxWarps + 1) * 32, Body::kMinBlocks)
   tile.failed = false;
   if constexpr (Body::kLayout == kLayoutSymbol) {
     tile.lane = (uint32_t)lane;
-    tile.seg = (uint32_t)warp * segment_bytes(W);
+    tile.seg = (uint32_t)warp * (uint32_t)Body::kGroups * segment_bytes(W);
   } else {
     tile.word = (uint32_t)(warp * 32 + lane);
     tile.span = ring.slice / (uint32_t)W;

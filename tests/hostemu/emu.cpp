@@ -45,6 +45,35 @@ struct HostTile {
   }
 };
 
+// G column groups per lane: lane l owns the 16-byte chunks at
+// l*16 + c*512 (c < G*W/4) of a segment of G*segment_bytes(W) bytes; group g
+// is words g*W .. g*W+W-1 (chunks g*W/4 ..), as the device's G-group tiles.
+template <int W, int G>
+struct HostTileG {
+  const uint8_t* const* in;
+  uint8_t* const* out;
+  size_t B;
+  size_t seg;
+  int lane;
+  void load(int i, uint32_t* x) {
+    for (int c = 0; c < G * W / 4; ++c) {
+      const size_t co = seg + (size_t)c * 512 + (size_t)lane * 16;
+      uint8_t b[16] = {0};
+      for (int t = 0; t < 16; ++t)
+        if (co + t < B) b[t] = in[i][co + t];
+      for (int q = 0; q < 4; ++q)
+        x[4 * c + q] = b[4 * q] | (b[4 * q + 1] << 8) | (b[4 * q + 2] << 16) | ((uint32_t)b[4 * q + 3] << 24);
+    }
+  }
+  void store(int t, const uint32_t* x) {
+    for (int c = 0; c < G * W / 4; ++c) {
+      const size_t co = seg + (size_t)c * 512 + (size_t)lane * 16;
+      for (int q = 0; q < 16; ++q)
+        if (co + q < B) out[t][co + q] = (uint8_t)(x[4 * c + q / 4] >> (8 * (q % 4)));
+    }
+  }
+};
+
 struct HostCoef {
   std::vector<uint32_t> words;
   explicit HostCoef(const DecodePlan* pl, int w) : words(pack_decode_selectors(*pl, w)) {}
@@ -77,6 +106,21 @@ void run_decode(const DecodePlan& pl, uint8_t* blocks, size_t B) {
     for (int lane = 0; lane < 32; ++lane) {
       HostTile<W> t{in.data(), out.data(), B, seg, lane};
       PolyDecode<W, M>::run(pl.n_pos, pl.read_mask, pl.e, t, t, cf);
+    }
+}
+
+template <int W, int M>
+void run_decode2(const DecodePlan& pl, uint8_t* blocks, size_t B) {
+  std::vector<const uint8_t*> in;
+  std::vector<uint8_t*> out;
+  for (int b : pl.in_blocks) in.push_back(blocks + (size_t)b * B);
+  for (int b : pl.out_blocks) out.push_back(blocks + (size_t)b * B);
+  const size_t segb = 2 * segment_bytes(W);
+  HostCoef cf(&pl, W);
+  for (size_t seg = 0; seg < B; seg += segb)
+    for (int lane = 0; lane < 32; ++lane) {
+      HostTileG<W, 2> t{in.data(), out.data(), B, seg, lane};
+      PolyDecode2<W, M>::run(pl.n_pos, pl.read_mask, pl.e, t, t, cf);
     }
 }
 
@@ -320,6 +364,22 @@ int emu_poly_decode(int w, int k, int m, const int* er, int e, int read_all, uin
   if (!make_poly_decode_plan(k, m, w, er, e, read_all != 0, pl, err)) return -1;
   if (e == 0) return 0;
   return w == 8 ? decode_w<8>(pl, blocks, B) : decode_w<16>(pl, blocks, B);
+}
+
+// The two-column-group decode (GF(2^8), M <= 4).
+int emu_poly_decode2(int w, int k, int m, const int* er, int e, int read_all, uint8_t* blocks, size_t B) {
+  DecodePlan pl;
+  std::string err;
+  if (w != 8) return -2;
+  if (!make_poly_decode_plan(k, m, w, er, e, read_all != 0, pl, err)) return -1;
+  if (e == 0) return 0;
+  switch (pl.M) {
+    case 1: run_decode2<8, 1>(pl, blocks, B); return 0;
+    case 2: run_decode2<8, 2>(pl, blocks, B); return 0;
+    case 3: run_decode2<8, 3>(pl, blocks, B); return 0;
+    case 4: run_decode2<8, 4>(pl, blocks, B); return 0;
+  }
+  return -2;
 }
 
 // Plan introspection for tests: M, read mask, W rows.

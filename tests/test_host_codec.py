@@ -113,3 +113,29 @@ def test_decode_seeded_patterns_match_oracle(emu, w, k, m, read_all):
         got[er] = 0x11
         _dec(emu, w, k, m, er, got, read_all)
         assert np.array_equal(got, ref), er
+
+
+@pytest.mark.parametrize("read_all", [False, True])
+@pytest.mark.parametrize("k,m,B", [(10, 4, 4096 + 48), (6, 3, 3000), (12, 4, 2048 + 7), (5, 2, 2048),
+                                   (20, 4, 9000), (3, 1, 100)])
+def test_two_group_decode_matches_oracle(emu, k, m, B, read_all):
+    """The decode with two 32-column groups per thread (GF(2^8), M <= 4)."""
+    emu.emu_poly_decode2.argtypes = [ctypes.c_int] * 3 + [ctypes.POINTER(ctypes.c_int), ctypes.c_int,
+                                                          ctypes.c_int, U8P, ctypes.c_size_t]
+    w, n = 8, k + m
+    base = np.zeros((n, B), dtype=np.uint8)
+    base[:k] = inputs.stripe_blocks(23, 0, k, B)
+    O.poly_encode(w, k, m, base)
+    pats = [p for e in range(1, m + 1) for p in itertools.combinations(range(n), e)]
+    rng = np.random.default_rng(k * 100 + m)
+    if len(pats) > 40:
+        pats = [pats[i] for i in rng.choice(len(pats), 40, replace=False)]
+    for er in pats:
+        got = base.copy()
+        got[list(er)] = 0x5A
+        arr = (ctypes.c_int * len(er))(*er)
+        rc = emu.emu_poly_decode2(w, k, m, arr, len(er), int(read_all), got.ctypes.data_as(U8P), B)
+        if rc == -2:  # M > 4 (read-all with fewer erasures keeps M <= e)
+            continue
+        assert rc == 0
+        assert np.array_equal(got, base), er
