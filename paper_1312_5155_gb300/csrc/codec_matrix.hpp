@@ -181,6 +181,51 @@ struct MatDecodeFixed {
   }
 };
 
+// Compile-time-P decode with two 32-column groups per thread (symbol
+// layout, M <= 4): the syndromes of both groups, then apply2_and_store.
+template <int W, int K, int M, int KIND>
+struct MatDecodeFixed2 {
+  template <class Src, class Dst, class Coef>
+  static RS_HD void run(uint64_t read_mask, int e, Src& src, Dst& dst, Coef& coef) {
+    Selectors<W, M> sel;
+    sel.load(coef);
+    uint32_t A[M][W], B[M][W];
+#pragma unroll
+    for (int i = 0; i < M; ++i)
+#pragma unroll
+      for (int b = 0; b < W; ++b) A[i][b] = B[i][b] = 0;
+    int in = 0;
+    StaticFor<0, K>::run([&](auto J) {
+      if ((read_mask >> decltype(J)::value) & 1ull) {
+        uint32_t x[2 * W];
+        src.load(in++, x);
+        transpose<W>(x);
+        transpose<W>(x + W);
+        StaticFor<0, M>::run([&](auto I) {
+          constexpr uint32_t c = ParityMatrix<W, K, M, KIND>::value.a[decltype(I)::value][decltype(J)::value];
+          mul_acc<W, c>(A[decltype(I)::value], x);
+          mul_acc<W, c>(B[decltype(I)::value], x + W);
+        });
+      }
+    });
+#pragma unroll
+    for (int j = 0; j < M; ++j) {
+      if ((read_mask >> (K + j)) & 1ull) {
+        uint32_t x[2 * W];
+        src.load(in++, x);
+        transpose<W>(x);
+        transpose<W>(x + W);
+#pragma unroll
+        for (int b = 0; b < W; ++b) {
+          A[j][b] ^= x[b];
+          B[j][b] ^= x[W + b];
+        }
+      }
+    }
+    apply2_and_store<W, M>(e, A, B, sel, dst);
+  }
+};
+
 // ------------------------------------------------ runtime P (any code)
 // cols.column(j) returns a PackedBits<W, M, 1> source for data column j of P
 // (entry (i, 0) = P[i][j]); the column's words are loaded before the input's

@@ -275,6 +275,48 @@ struct PolyDecode {
   }
 };
 
+// apply_and_store for two 32-column groups (symbol layout): output t of
+// group 0 from the syndromes A, of group 1 from B, stored as one 2W-word
+// output (group 0 in words 0..W-1).  M <= 4, no pair sums.
+template <int W, int M, class Dst>
+RS_HD void apply2_and_store(int e, const uint32_t (*A)[W], const uint32_t (*B)[W], const Selectors<W, M>& sel,
+                            Dst& dst) {
+  static_assert(M <= 4, "one selector chunk");
+  using Sel = Selectors<W, M>;
+#pragma unroll 1
+  for (int t = 0; t < e; ++t) {
+    uint32_t row[Sel::kRowWords];
+    sel.row(t, row);
+    uint32_t y[2 * W];
+#pragma unroll
+    for (int b = 0; b < 2 * W; ++b) y[b] = 0;
+    constexpr int kSteps = kApplySteps<W>;
+#pragma unroll 1
+    for (int c0 = W - 1; c0 >= 0; c0 -= kSteps) {
+      StaticFor<0, kSteps>::run([&](auto Uu) {
+        constexpr int u = decltype(Uu)::value;
+        const int c = c0 - u;
+        mul_alpha_renamed<W, u>(y);
+        mul_alpha_renamed<W, u>(y + W);
+        xor_selected2<W, u + 1, M>(Sel::nibble(row, c), y, y + W, A, B);
+      });
+      if constexpr (kSteps % W != 0) {
+        uint32_t r[2 * W];
+#pragma unroll
+        for (int b = 0; b < W; ++b) {
+          r[b] = y[((b - kSteps) % W + W) % W];
+          r[W + b] = y[W + ((b - kSteps) % W + W) % W];
+        }
+#pragma unroll
+        for (int b = 0; b < 2 * W; ++b) y[b] = r[b];
+      }
+    }
+    transpose<W>(y);
+    transpose<W>(y + W);
+    dst.store(t, y);
+  }
+}
+
 // Two 32-column groups per thread (G = 2): the same decode as PolyDecode on
 // 2W words (group 0 = words 0..W-1, group 1 = W..2W-1 of every input and
 // output).  Every warp-uniform decision -- the Horner presence test, the
@@ -336,40 +378,7 @@ struct PolyDecode2 {
         });
       }
     }
-    // erased outputs, one at a time (as apply_and_store, both groups)
-    using Sel = Selectors<W, M>;
-#pragma unroll 1
-    for (int t = 0; t < e; ++t) {
-      uint32_t row[Sel::kRowWords];
-      sel.row(t, row);
-      uint32_t y[2 * W];
-#pragma unroll
-      for (int b = 0; b < 2 * W; ++b) y[b] = 0;
-      constexpr int kSteps = kApplySteps<W>;
-#pragma unroll 1
-      for (int c0 = W - 1; c0 >= 0; c0 -= kSteps) {
-        StaticFor<0, kSteps>::run([&](auto Uu) {
-          constexpr int u = decltype(Uu)::value;
-          const int c = c0 - u;
-          mul_alpha_renamed<W, u>(y);
-          mul_alpha_renamed<W, u>(y + W);
-          xor_selected2<W, u + 1, M>(Sel::nibble(row, c), y, y + W, A, B);
-        });
-        if constexpr (kSteps % W != 0) {
-          uint32_t r[2 * W];
-#pragma unroll
-          for (int b = 0; b < W; ++b) {
-            r[b] = y[((b - kSteps) % W + W) % W];
-            r[W + b] = y[W + ((b - kSteps) % W + W) % W];
-          }
-#pragma unroll
-          for (int b = 0; b < 2 * W; ++b) y[b] = r[b];
-        }
-      }
-      transpose<W>(y);
-      transpose<W>(y + W);
-      dst.store(t, y);
-    }
+    apply2_and_store<W, M>(e, A, B, sel, dst);
   }
 };
 

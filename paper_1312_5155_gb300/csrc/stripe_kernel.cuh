@@ -392,6 +392,25 @@ struct MatFixedBody {
   }
 };
 
+// Compile-time-P decode (symbol layout, M <= 4) with two 32-column groups
+// per lane (MatDecodeFixed2); register budget as PolyDecode2Body.
+template <int W, int K, int M, int KIND>
+struct MatFixedDecode2Body {
+  static constexpr int kW = W;
+  static constexpr int kGroups = 2;
+  static constexpr int kLayout = kLayoutSymbol;
+  static constexpr int kMaxOut = M;
+  static constexpr int kMaxWarps = 12;
+  static constexpr int kMinBlocks = 1;
+  static_assert(kind_layout(KIND) == kLayoutSymbol, "symbol-layout kinds only");
+  __device__ static bool matches(const TileOp& o) { return o.op == kOpMatDecode && o.m == M && o.k == K; }
+  template <class Tile>
+  __device__ static void run(const TileOp& o, Tile& t, const uint32_t* coef) {
+    CoefWords cm{coef};
+    MatDecodeFixed2<W, K, M, KIND>::run(o.read_mask, o.e, t, t, cm);
+  }
+};
+
 // Several bodies of the same width and layout in one kernel: each stripe
 // runs the first body whose matches() accepts it.
 template <class First, class... Rest>

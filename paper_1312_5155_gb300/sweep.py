@@ -42,7 +42,7 @@ from . import autotune, inputs, rs
 GIB = 1 << 30
 # launch shapes tried per case (consumer warps, ring depth, CTAs per SM): the
 # ones the bench's autotuner picks for these kernels
-SHAPES = [(16, 8, 1), (16, 12, 1), (12, 6, 1), (8, 12, 2), (8, 8, 2)]
+SHAPES = [(16, 8, 1), (16, 12, 1), (12, 4, 1), (12, 6, 1), (8, 12, 2), (8, 8, 2)]
 
 
 def _torch():

@@ -248,6 +248,23 @@ int mat_fixed(bool decode, const DecodePlan* pl, uint8_t* blocks, size_t B, size
   return 0;
 }
 
+// The two-column-group compile-time-P decode (symbol layout).
+template <int W, int K, int M, int KIND>
+int mat_fixed2(const DecodePlan* pl, uint8_t* blocks, size_t B) {
+  std::vector<const uint8_t*> in;
+  std::vector<uint8_t*> out;
+  for (int b : pl->in_blocks) in.push_back(blocks + (size_t)b * B);
+  for (int b : pl->out_blocks) out.push_back(blocks + (size_t)b * B);
+  HostCoef cf(pl, W);
+  const size_t segb = 2 * segment_bytes(W);
+  for (size_t seg = 0; seg < B; seg += segb)
+    for (int lane = 0; lane < 32; ++lane) {
+      HostTileG<W, 2> t{in.data(), out.data(), B, seg, lane};
+      MatDecodeFixed2<W, K, M, KIND>::run(pl->read_mask, pl->e, t, t, cf);
+    }
+  return 0;
+}
+
 template <int W, bool kPacket>
 int mat_runtime_m(int k, int m, const std::vector<uint32_t>& P, bool decode, const DecodePlan* pl, uint8_t* blocks,
                   size_t B, size_t pkt) {
@@ -321,6 +338,26 @@ int emu_mat(int w, int k, int m, int kind, int fixed, const int* er, int e, int 
                             : mat_runtime_m<8, false>(k, m, P, decode, plp, blocks, B, pkt);
   return packet ? mat_runtime_m<16, true>(k, m, P, decode, plp, blocks, B, pkt)
                 : mat_runtime_m<16, false>(k, m, P, decode, plp, blocks, B, pkt);
+}
+
+// Two-column-group matrix decode (GF(2^8), symbol-layout kinds 1 and 3).
+int emu_mat_decode2(int w, int k, int m, int kind, const int* er, int e, int read_all, uint8_t* blocks, size_t B) {
+  if (w != 8 || (kind != 1 && kind != 3) || e <= 0) return -2;
+  std::vector<uint32_t> P;
+  if (!host_parity(w, k, m, kind, P)) return -3;
+  DecodePlan pl;
+  std::string err;
+  if (!make_matrix_decode_plan(k, m, w, P, er, e, read_all != 0, pl, err)) return -1;
+  if (pl.M > 4) return -2;
+  if (kind == 1) {
+    if (k == 10 && m == 4) return mat_fixed2<8, 10, 4, 1>(&pl, blocks, B);
+    if (k == 6 && m == 3) return mat_fixed2<8, 6, 3, 1>(&pl, blocks, B);
+    if (k == 20 && m == 4) return mat_fixed2<8, 20, 4, 1>(&pl, blocks, B);
+  } else {
+    if (k == 10 && m == 4) return mat_fixed2<8, 10, 4, 3>(&pl, blocks, B);
+    if (k == 6 && m == 3) return mat_fixed2<8, 6, 3, 3>(&pl, blocks, B);
+  }
+  return -2;
 }
 
 // Host copy of the parity matrix the library builds (for the tests).

@@ -131,3 +131,27 @@ def test_decode_every_pattern_rs_6_3(emu, real):
                 got[list(er)] = 0
                 run(emu, real, w, k, m, fixed, list(er), got, pkt, read_all=(e % 2 == 0))
                 assert np.array_equal(got, base), (er, fixed)
+
+
+@pytest.mark.parametrize("read_all", [False, True])
+@pytest.mark.parametrize("real,k,m,B", [("vandermonde", 10, 4, 4096 + 48), ("vandermonde", 6, 3, 3000),
+                                        ("vandermonde", 20, 4, 2048 + 5), ("poly_matrix", 10, 4, 3000),
+                                        ("poly_matrix", 6, 3, 100)])
+def test_two_group_matrix_decode_matches_oracle(emu, real, k, m, B, read_all):
+    """The compile-time-P decode with two 32-column groups per thread."""
+    emu.emu_mat_decode2.argtypes = [ctypes.c_int] * 4 + [ctypes.POINTER(ctypes.c_int), ctypes.c_int, ctypes.c_int,
+                                                         U8P, ctypes.c_size_t]
+    w, n = 8, k + m
+    base = make_stripe(w, k, m, B)
+    O.encode(real, w, k, m, base)
+    pats = [p for e in range(1, m + 1) for p in itertools.combinations(range(n), e)]
+    rng = np.random.default_rng(k * 10 + m)
+    if len(pats) > 40:
+        pats = [pats[i] for i in rng.choice(len(pats), 40, replace=False)]
+    for er in pats:
+        got = base.copy()
+        got[list(er)] = 0x77
+        arr = (ctypes.c_int * len(er))(*er)
+        rc = emu.emu_mat_decode2(w, k, m, KIND[real], arr, len(er), int(read_all), got.ctypes.data_as(U8P), B)
+        assert rc == 0, rc
+        assert np.array_equal(got, base), er
