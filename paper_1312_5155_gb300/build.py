@@ -63,9 +63,13 @@ def instances():
     for (w, k, m), kind in fixed:
         for op in (2, 3):
             layout = 1 if kind in (2, 4) else 0
-            # symbol-layout GF(2^8) decodes with m <= 4: two column groups per lane
+            # symbol-layout GF(2^8) codes with m <= 4: two column groups per lane
+            # (measured faster for these encodes and decodes; the LFSR encode
+            # keeps one)
             two = op == 3 and layout == 0 and w == 8 and m <= 4
-            body = f"MatFixedDecode2Body<{w}, {k}, {m}, {kind}>" if two else f"MatFixedBody<{w}, {k}, {m}, {kind}, {op}>"
+            two_enc = op == 2 and layout == 0 and w == 8 and m <= 4
+            body = (f"MatFixedDecode2Body<{w}, {k}, {m}, {kind}>" if two else
+                    f"MatFixedEncode2Body<{w}, {k}, {m}, {kind}>" if two_enc else f"MatFixedBody<{w}, {k}, {m}, {kind}, {op}>")
             out.append((f"matfix_w{w}_k{k}_m{m}_kind{kind}_op{op}", body,
                         dict(family=2, w=w, m=m, op=op, layout=layout, kind=kind, k=k)))
     for (w, ms) in MIXED_POLY:

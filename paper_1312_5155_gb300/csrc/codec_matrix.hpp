@@ -143,6 +143,42 @@ struct MatEncodeFixed {
   }
 };
 
+// Compile-time-P encode on two 32-column groups per thread (symbol layout).
+template <int W, int K, int M, int KIND>
+struct MatEncodeFixed2 {
+  template <class Src, class Dst>
+  static RS_HD void run(Src& src, Dst& dst) {
+    uint32_t a[M][W], b[M][W];
+#pragma unroll
+    for (int i = 0; i < M; ++i)
+#pragma unroll
+      for (int c = 0; c < W; ++c) a[i][c] = b[i][c] = 0;
+    StaticFor<0, K>::run([&](auto J) {
+      uint32_t x[2 * W];
+      src.load(decltype(J)::value, x);
+      transpose<W>(x);
+      transpose<W>(x + W);
+      StaticFor<0, M>::run([&](auto I) {
+        constexpr uint32_t c = ParityMatrix<W, K, M, KIND>::value.a[decltype(I)::value][decltype(J)::value];
+        mul_acc<W, c>(a[decltype(I)::value], x);
+        mul_acc<W, c>(b[decltype(I)::value], x + W);
+      });
+    });
+#pragma unroll
+    for (int i = 0; i < M; ++i) {
+      uint32_t y[2 * W];
+#pragma unroll
+      for (int c = 0; c < W; ++c) {
+        y[c] = a[i][c];
+        y[W + c] = b[i][c];
+      }
+      transpose<W>(y);
+      transpose<W>(y + W);
+      dst.store(i, y);
+    }
+  }
+};
+
 // ------------------------------------------------ compile-time P: decode
 template <int W, int K, int M, int KIND, bool kTranspose>
 struct MatDecodeFixed {

@@ -331,6 +331,24 @@ struct PolyBody {
   }
 };
 
+// Compile-time-P encode with two 32-column groups per lane (symbol layout,
+// GF(2^8), M <= 4): MatEncodeFixed2.
+template <int W, int K, int M, int KIND>
+struct MatFixedEncode2Body {
+  static constexpr int kW = W;
+  static constexpr int kGroups = 2;
+  static constexpr int kLayout = kLayoutSymbol;
+  static constexpr int kMaxOut = M;
+  static constexpr int kMaxWarps = 12;
+  static constexpr int kMinBlocks = 1;
+  static_assert(kind_layout(KIND) == kLayoutSymbol, "symbol-layout kinds only");
+  __device__ static bool matches(const TileOp& o) { return o.op == kOpMatEncode && o.m == M && o.k == K; }
+  template <class Tile>
+  __device__ static void run(const TileOp&, Tile& t, const uint32_t*) {
+    MatEncodeFixed2<W, K, M, KIND>::run(t, t);
+  }
+};
+
 // GF(2^8) polynomial decode with two 32-column groups per lane
 // (PolyDecode2): 64 columns per thread share every warp-uniform decision.
 template <int W, int M>

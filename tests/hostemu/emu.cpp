@@ -265,6 +265,21 @@ int mat_fixed2(const DecodePlan* pl, uint8_t* blocks, size_t B) {
   return 0;
 }
 
+template <int K, int M, int KIND>
+int mat_encode2(uint8_t* blocks, size_t B) {
+  std::vector<const uint8_t*> in;
+  std::vector<uint8_t*> out;
+  for (int j = 0; j < K; ++j) in.push_back(blocks + (size_t)j * B);
+  for (int i = 0; i < M; ++i) out.push_back(blocks + (size_t)(K + i) * B);
+  const size_t segb = 2 * segment_bytes(8);
+  for (size_t seg = 0; seg < B; seg += segb)
+    for (int lane = 0; lane < 32; ++lane) {
+      HostTileG<8, 2> t{in.data(), out.data(), B, seg, lane};
+      MatEncodeFixed2<8, K, M, KIND>::run(t, t);
+    }
+  return 0;
+}
+
 template <int W, bool kPacket>
 int mat_runtime_m(int k, int m, const std::vector<uint32_t>& P, bool decode, const DecodePlan* pl, uint8_t* blocks,
                   size_t B, size_t pkt) {
@@ -401,6 +416,15 @@ int emu_poly_decode(int w, int k, int m, const int* er, int e, int read_all, uin
   if (!make_poly_decode_plan(k, m, w, er, e, read_all != 0, pl, err)) return -1;
   if (e == 0) return 0;
   return w == 8 ? decode_w<8>(pl, blocks, B) : decode_w<16>(pl, blocks, B);
+}
+
+// The two-column-group compile-time-P encodes (GF(2^8), M <= 4): kinds 1
+// and 3 (Vandermonde, generator-matrix form of the polynomial code).
+int emu_encode2(int kind, int k, int m, uint8_t* blocks, size_t B) {
+  if (kind == 1 && k == 10 && m == 4) return mat_encode2<10, 4, 1>(blocks, B);
+  if (kind == 1 && k == 6 && m == 3) return mat_encode2<6, 3, 1>(blocks, B);
+  if (kind == 3 && k == 10 && m == 4) return mat_encode2<10, 4, 3>(blocks, B);
+  return -2;
 }
 
 // The two-column-group decode (GF(2^8), M <= 4).

@@ -139,3 +139,20 @@ def test_two_group_decode_matches_oracle(emu, k, m, B, read_all):
             continue
         assert rc == 0
         assert np.array_equal(got, base), er
+
+
+@pytest.mark.parametrize("real,k,m,B", [("vandermonde", 10, 4, 4096 + 16), ("vandermonde", 6, 3, 3000),
+                                        ("poly_matrix", 10, 4, 5000), ("poly_matrix", 10, 4, 100)])
+def test_two_group_encode_matches_oracle(emu, real, k, m, B):
+    """The compile-time-P encodes with two 32-column groups per thread."""
+    emu.emu_encode2.argtypes = [ctypes.c_int] * 3 + [U8P, ctypes.c_size_t]
+    kind = {"vandermonde": 1, "poly_matrix": 3}[real]
+    w = 8
+    base = np.zeros((k + m, B), dtype=np.uint8)
+    base[:k] = inputs.stripe_blocks(29, 0, k, B)
+    ref = base.copy()
+    O.encode(real, w, k, m, ref)
+    got = base.copy()
+    got[k:] = 0x3C
+    assert emu.emu_encode2(kind, k, m, got.ctypes.data_as(U8P), B) == 0
+    assert np.array_equal(got, ref)
