@@ -63,10 +63,10 @@ def instances():
     for (w, k, m), kind in fixed:
         for op in (2, 3):
             layout = 1 if kind in (2, 4) else 0
-            # symbol-layout GF(2^8) codes with m <= 4: two column groups per lane
-            # (measured faster for these encodes and decodes; the LFSR encode
-            # keeps one)
-            two = op == 3 and layout == 0 and w == 8 and m <= 4
+            # GF(2^8) codes with m <= 4: two column groups per lane (measured
+            # faster for these decodes in both layouts and for the
+            # symbol-layout encodes; the LFSR encode keeps one)
+            two = op == 3 and w == 8 and m <= 4
             two_enc = op == 2 and layout == 0 and w == 8 and m <= 4
             body = (f"MatFixedDecode2Body<{w}, {k}, {m}, {kind}>" if two else
                     f"MatFixedEncode2Body<{w}, {k}, {m}, {kind}>" if two_enc else f"MatFixedBody<{w}, {k}, {m}, {kind}, {op}>")

@@ -172,6 +172,16 @@ rs_status select_kernel(const rs_code* c, int op, int M, PreparedOp& po) {
   }
   po.key = key;
   po.entry = find_kernel(key);
+  // a two-group packet kernel needs tiles of at least 256 bytes per packet
+  // row: smaller packets take the runtime-matrix kernel
+  if (po.entry && key.layout == kLayoutPacket && po.entry->groups > 1 &&
+      c->packet_bytes % (size_t)(128 * po.entry->groups)) {
+    key.family = kFamMatRuntime;
+    key.kind = 0;
+    key.k = 0;
+    po.key = key;
+    po.entry = find_kernel(key);
+  }
   if (!po.entry) return fail(RS_EUNSUPPORTED, "no kernel compiled for this code");
   return RS_OK;
 }
@@ -283,12 +293,12 @@ rs_status prepare_decode(rs_code* c, const int* er, int e, void* const* blocks, 
 }
 
 // Consumer warps for a launch: the tuned value capped by the kernel; in
-// the packet layout a tile spans nc*128 bytes of a packet, which must
-// divide every packet size of the launch.
-int pick_warps(const TuneCfg& t, int cap, int layout, uint32_t packet_gcd) {
+// the packet layout a tile spans nc*128*groups bytes of a packet, which
+// must divide every packet size of the launch.
+int pick_warps(const TuneCfg& t, int cap, int groups, int layout, uint32_t packet_gcd) {
   int nc = std::max(1, std::min(t.consumer_warps, cap));
   if (layout == kLayoutPacket)
-    while (nc > 1 && packet_gcd % (uint32_t)(nc * 128)) --nc;
+    while (nc > 1 && packet_gcd % (uint32_t)(nc * 128 * groups)) --nc;
   return nc;
 }
 
@@ -314,7 +324,7 @@ rs_status launch_single(rs_code* c, PreparedOp& po, void* stream) {
   if (s != RS_OK) return s;
   JobParams* p = new (std::nothrow) JobParams();
   if (!p) return fail(RS_ENOMEM, "host allocation failed");
-  const int nc = pick_warps(c->tune, po.entry->max_warps, po.key.layout, po.d.packet_bytes);
+  const int nc = pick_warps(c->tune, po.entry->max_warps, po.entry->groups, po.key.layout, po.d.packet_bytes);
   uint32_t slice, depth;
   LaunchShape sh = make_shape(c->tune, nc, c->w, po.entry->groups, c->num_sms, slice, depth);
   p->status = c->d_status;
@@ -683,7 +693,7 @@ rs_status rs_batch_set(rs_batch* b, const rs_op* ops, int n_ops, void* stream) {
       pg = a;
     }
     gr.layout = layout;
-    gr.nc = pick_warps(b->tune, gr.entry->max_warps, layout, pg);
+    gr.nc = pick_warps(b->tune, gr.entry->max_warps, gr.entry->groups, layout, pg);
     const int w = gr.entry->key.w;
     gr.sh = make_shape(b->tune, gr.nc, w, gr.entry->groups, b->num_sms, gr.slice, gr.depth);
     uint32_t tiles = 0;

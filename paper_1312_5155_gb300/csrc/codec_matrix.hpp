@@ -217,9 +217,9 @@ struct MatDecodeFixed {
   }
 };
 
-// Compile-time-P decode with two 32-column groups per thread (symbol
-// layout, M <= 4): the syndromes of both groups, then apply2_and_store.
-template <int W, int K, int M, int KIND>
+// Compile-time-P decode with two 32-column groups per thread (M <= 4): the
+// syndromes of both groups, then apply2_and_store.
+template <int W, int K, int M, int KIND, bool kTranspose = true>
 struct MatDecodeFixed2 {
   template <class Src, class Dst, class Coef>
   static RS_HD void run(uint64_t read_mask, int e, Src& src, Dst& dst, Coef& coef) {
@@ -235,8 +235,10 @@ struct MatDecodeFixed2 {
       if ((read_mask >> decltype(J)::value) & 1ull) {
         uint32_t x[2 * W];
         src.load(in++, x);
-        transpose<W>(x);
-        transpose<W>(x + W);
+        if (kTranspose) {
+          transpose<W>(x);
+          transpose<W>(x + W);
+        }
         StaticFor<0, M>::run([&](auto I) {
           constexpr uint32_t c = ParityMatrix<W, K, M, KIND>::value.a[decltype(I)::value][decltype(J)::value];
           mul_acc<W, c>(A[decltype(I)::value], x);
@@ -249,8 +251,10 @@ struct MatDecodeFixed2 {
       if ((read_mask >> (K + j)) & 1ull) {
         uint32_t x[2 * W];
         src.load(in++, x);
-        transpose<W>(x);
-        transpose<W>(x + W);
+        if (kTranspose) {
+          transpose<W>(x);
+          transpose<W>(x + W);
+        }
 #pragma unroll
         for (int b = 0; b < W; ++b) {
           A[j][b] ^= x[b];
@@ -258,7 +262,7 @@ struct MatDecodeFixed2 {
         }
       }
     }
-    apply2_and_store<W, M>(e, A, B, sel, dst);
+    apply2_and_store<W, M, kTranspose>(e, A, B, sel, dst);
   }
 };
 

@@ -275,10 +275,11 @@ struct PolyDecode {
   }
 };
 
-// apply_and_store for two 32-column groups (symbol layout): output t of
-// group 0 from the syndromes A, of group 1 from B, stored as one 2W-word
-// output (group 0 in words 0..W-1).  M <= 4, no pair sums.
-template <int W, int M, class Dst>
+// apply_and_store for two 32-column groups: output t of group 0 from the
+// syndromes A, of group 1 from B, stored as one 2W-word output (group 0 in
+// words 0..W-1; planes back to symbols with kTranspose).  M <= 4, no pair
+// sums.
+template <int W, int M, bool kTranspose = true, class Dst>
 RS_HD void apply2_and_store(int e, const uint32_t (*A)[W], const uint32_t (*B)[W], const Selectors<W, M>& sel,
                             Dst& dst) {
   static_assert(M <= 4, "one selector chunk");
@@ -311,8 +312,10 @@ RS_HD void apply2_and_store(int e, const uint32_t (*A)[W], const uint32_t (*B)[W
         for (int b = 0; b < 2 * W; ++b) y[b] = r[b];
       }
     }
-    transpose<W>(y);
-    transpose<W>(y + W);
+    if (kTranspose) {
+      transpose<W>(y);
+      transpose<W>(y + W);
+    }
     dst.store(t, y);
   }
 }

@@ -238,8 +238,12 @@ struct SymTile {
   }
 };
 
-template <int W, int MO>
+// G column groups per lane: lane `word` owns the G adjacent 32-bit words
+// G*word .. G*word+G-1 of every packet row of the span; group g is words
+// g*W .. g*W+W-1 of a load or store (word g of each of the W rows).
+template <int W, int MO, int G = 1>
 struct PacketTile {
+  static_assert(G == 1 || G == 2, "one or two groups");
   Ring* ring;
   const uint64_t* ptrs;
   uint64_t outp[MO];  // output pointers, loaded at tile start
@@ -248,7 +252,7 @@ struct PacketTile {
   uint32_t span_off;  // offset inside each packet
   uint32_t span;      // bytes per packet row in the slot
   uint32_t P;         // packet bytes
-  uint32_t word;      // this thread's 32-bit word inside the span
+  uint32_t word;      // this thread's first 32-bit word group inside the span
   int* status;
   unsigned long long limit;
   bool failed;
@@ -269,17 +273,31 @@ struct PacketTile {
     r.advance();
     wait_or_fail(&r.full[s], par, failed, status, kDevErrTimeoutFull, limit);
     const uint8_t* slot = r.slots + (size_t)s * r.slice;
+    // stale after a timed-out wait; store() then writes nothing
+    if constexpr (G == 1) {
 #pragma unroll
-    for (int c = 0; c < W; ++c)  // stale after a timed-out wait; store() then writes nothing
-      x[c] = *reinterpret_cast<const uint32_t*>(slot + (size_t)c * span + 4u * word);
+      for (int c = 0; c < W; ++c) x[c] = *reinterpret_cast<const uint32_t*>(slot + (size_t)c * span + 4u * word);
+    } else {
+#pragma unroll
+      for (int c = 0; c < W; ++c) {
+        const uint2 v = *reinterpret_cast<const uint2*>(slot + (size_t)c * span + 8u * word);
+        x[c] = v.x;
+        x[W + c] = v.y;
+      }
+    }
     mbar_arrive(&r.empty[s]);
   }
 
   __device__ __forceinline__ void store(int t, const uint32_t* x) {
     if (failed) return;
-    uint8_t* out = reinterpret_cast<uint8_t*>(select_out(outp, t)) + goff + span_off + 4u * word;
+    uint8_t* out = reinterpret_cast<uint8_t*>(select_out(outp, t)) + goff + span_off + 4u * G * word;
+    if constexpr (G == 1) {
 #pragma unroll
-    for (int c = 0; c < W; ++c) *reinterpret_cast<uint32_t*>(out + (size_t)c * P) = x[c];
+      for (int c = 0; c < W; ++c) *reinterpret_cast<uint32_t*>(out + (size_t)c * P) = x[c];
+    } else {
+#pragma unroll
+      for (int c = 0; c < W; ++c) *reinterpret_cast<uint2*>(out + (size_t)c * P) = make_uint2(x[c], x[W + c]);
+    }
   }
 };
 
@@ -410,22 +428,23 @@ struct MatFixedBody {
   }
 };
 
-// Compile-time-P decode (symbol layout, M <= 4) with two 32-column groups
-// per lane (MatDecodeFixed2); register budget as PolyDecode2Body.
+// Compile-time-P decode (M <= 4) with two 32-column groups per lane
+// (MatDecodeFixed2), in either layout.
 template <int W, int K, int M, int KIND>
 struct MatFixedDecode2Body {
   static constexpr int kW = W;
   static constexpr int kGroups = 2;
-  static constexpr int kLayout = kLayoutSymbol;
+  static constexpr int kLayout = kind_layout(KIND);
   static constexpr int kMaxOut = M;
-  static constexpr int kMaxWarps = 12;
+  // symbol layout: 12 warps at 128 registers; packet layout: a tile's span
+  // (warps x 256 bytes) must divide the packet, so at most 8 warps
+  static constexpr int kMaxWarps = kLayout == kLayoutSymbol ? 12 : 8;
   static constexpr int kMinBlocks = 1;
-  static_assert(kind_layout(KIND) == kLayoutSymbol, "symbol-layout kinds only");
   __device__ static bool matches(const TileOp& o) { return o.op == kOpMatDecode && o.m == M && o.k == K; }
   template <class Tile>
   __device__ static void run(const TileOp& o, Tile& t, const uint32_t* coef) {
     CoefWords cm{coef};
-    MatDecodeFixed2<W, K, M, KIND>::run(o.read_mask, o.e, t, t, cm);
+    MatDecodeFixed2<W, K, M, KIND, kind_layout(KIND) == kLayoutSymbol>::run(o.read_mask, o.e, t, t, cm);
   }
 };
 
@@ -609,9 +628,8 @@ __global__ void __launch_bounds__((Body::kMaxWarps + 1) * 32, Body::kMinBlocks)
     return;
   }
 
-  static_assert(Body::kLayout == kLayoutSymbol || Body::kGroups == 1, "packet tiles have one group");
   using Tile = std::conditional_t<Body::kLayout == kLayoutSymbol, SymTile<W, Body::kMaxOut, Body::kGroups>,
-                                  PacketTile<W, Body::kMaxOut>>;
+                                  PacketTile<W, Body::kMaxOut, Body::kGroups>>;
   Tile tile;
   tile.ring = &ring;
   tile.status = p.status;

@@ -265,6 +265,47 @@ int mat_fixed2(const DecodePlan* pl, uint8_t* blocks, size_t B) {
   return 0;
 }
 
+// Packet layout with two groups: the thread owns words 2u and 2u + 1 of the
+// W packets of one super-packet; group g is word 2u + g of each packet.
+template <int W>
+struct HostPacketTile2 {
+  const uint8_t* const* in;
+  uint8_t* const* out;
+  size_t sp_off;
+  size_t P;
+  size_t u;
+  void load(int i, uint32_t* x) {
+    for (int g = 0; g < 2; ++g)
+      for (int c = 0; c < W; ++c) {
+        const uint8_t* p = in[i] + sp_off + (size_t)c * P + 4 * (2 * u + g);
+        x[g * W + c] = p[0] | (p[1] << 8) | (p[2] << 16) | ((uint32_t)p[3] << 24);
+      }
+  }
+  void store(int t, const uint32_t* x) {
+    for (int g = 0; g < 2; ++g)
+      for (int c = 0; c < W; ++c) {
+        uint8_t* p = out[t] + sp_off + (size_t)c * P + 4 * (2 * u + g);
+        for (int q = 0; q < 4; ++q) p[q] = (uint8_t)(x[g * W + c] >> (8 * q));
+      }
+  }
+};
+
+// The two-column-group compile-time-P decode in the packet layout.
+template <int W, int K, int M, int KIND>
+int mat_fixed2_packet(const DecodePlan* pl, uint8_t* blocks, size_t B, size_t P) {
+  std::vector<const uint8_t*> in;
+  std::vector<uint8_t*> out;
+  for (int b : pl->in_blocks) in.push_back(blocks + (size_t)b * B);
+  for (int b : pl->out_blocks) out.push_back(blocks + (size_t)b * B);
+  HostCoef cf(pl, W);
+  for (size_t sp = 0; sp < B; sp += (size_t)W * P)
+    for (size_t u = 0; u < P / 8; ++u) {
+      HostPacketTile2<W> t{in.data(), out.data(), sp, P, u};
+      MatDecodeFixed2<W, K, M, KIND, false>::run(pl->read_mask, pl->e, t, t, cf);
+    }
+  return 0;
+}
+
 template <int K, int M, int KIND>
 int mat_encode2(uint8_t* blocks, size_t B) {
   std::vector<const uint8_t*> in;
@@ -371,6 +412,26 @@ int emu_mat_decode2(int w, int k, int m, int kind, const int* er, int e, int rea
   } else {
     if (k == 10 && m == 4) return mat_fixed2<8, 10, 4, 3>(&pl, blocks, B);
     if (k == 6 && m == 3) return mat_fixed2<8, 6, 3, 3>(&pl, blocks, B);
+  }
+  return -2;
+}
+
+// Two-column-group matrix decode in the packet layout (GF(2^8), kinds 2 and
+// 4; P = packet bytes, a multiple of 8 dividing B / 8).
+int emu_mat_decode2_packet(int w, int k, int m, int kind, const int* er, int e, int read_all, uint8_t* blocks,
+                           size_t B, size_t P) {
+  if (w != 8 || (kind != 2 && kind != 4) || e <= 0 || P % 8 || B % (8 * P)) return -2;
+  std::vector<uint32_t> Pm;
+  if (!host_parity(w, k, m, kind, Pm)) return -3;
+  DecodePlan pl;
+  std::string err;
+  if (!make_matrix_decode_plan(k, m, w, Pm, er, e, read_all != 0, pl, err)) return -1;
+  if (pl.M > 4) return -2;
+  if (kind == 2) {
+    if (k == 10 && m == 4) return mat_fixed2_packet<8, 10, 4, 2>(&pl, blocks, B, P);
+    if (k == 6 && m == 3) return mat_fixed2_packet<8, 6, 3, 2>(&pl, blocks, B, P);
+  } else {
+    if (k == 10 && m == 4) return mat_fixed2_packet<8, 10, 4, 4>(&pl, blocks, B, P);
   }
   return -2;
 }

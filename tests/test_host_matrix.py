@@ -155,3 +155,29 @@ def test_two_group_matrix_decode_matches_oracle(emu, real, k, m, B, read_all):
         rc = emu.emu_mat_decode2(w, k, m, KIND[real], arr, len(er), int(read_all), got.ctypes.data_as(U8P), B)
         assert rc == 0, rc
         assert np.array_equal(got, base), er
+
+
+@pytest.mark.parametrize("read_all", [False, True])
+@pytest.mark.parametrize("real,k,m,pkt,sp", [("cauchy", 10, 4, 256, 3), ("cauchy", 6, 3, 2048, 1),
+                                             ("poly_bitmatrix", 10, 4, 512, 2)])
+def test_two_group_packet_decode_matches_oracle(emu, real, k, m, pkt, sp, read_all):
+    """The packet-layout compile-time-P decode with two adjacent words per
+    thread (one 64-bit load per packet row)."""
+    emu.emu_mat_decode2_packet.argtypes = [ctypes.c_int] * 4 + [ctypes.POINTER(ctypes.c_int), ctypes.c_int,
+                                                                ctypes.c_int, U8P, ctypes.c_size_t, ctypes.c_size_t]
+    w, n = 8, k + m
+    B = sp * w * pkt
+    base = make_stripe(w, k, m, B)
+    O.encode(real, w, k, m, base, packet_bytes=pkt)
+    pats = [p for e in range(1, m + 1) for p in itertools.combinations(range(n), e)]
+    rng = np.random.default_rng(k * 100 + m + pkt)
+    if len(pats) > 30:
+        pats = [pats[i] for i in rng.choice(len(pats), 30, replace=False)]
+    for er in pats:
+        got = base.copy()
+        got[list(er)] = 0x5A
+        arr = (ctypes.c_int * len(er))(*er)
+        rc = emu.emu_mat_decode2_packet(w, k, m, KIND[real], arr, len(er), int(read_all), got.ctypes.data_as(U8P),
+                                        B, pkt)
+        assert rc == 0, rc
+        assert np.array_equal(got, base), er
