@@ -3,7 +3,9 @@
 A launch shape is (consumer warps per CTA, ring depth, CTAs per SM):
   - consumer warps set the tile width: a tile covers consumer_warps x 32
     threads x 32 columns of every block (1 KiB per warp at w = 8,
-    2 KiB at w = 16), and every thread owns 32 columns;
+    2 KiB at w = 16), and every thread owns 32 columns (64 in the
+    two-group kernels); the kernel caps the count at what its registers
+    allow;
   - ring depth is how many block slices are in flight per CTA (the unroll
     depth of the shared-memory pipeline);
   - CTAs per SM sets the persistent grid (SMs x CTAs per SM).
@@ -18,8 +20,8 @@ import math
 import os
 import threading
 
-CANDIDATES = [(16, 8, 1), (16, 12, 1), (12, 6, 1), (12, 4, 1), (12, 3, 1), (8, 16, 1), (8, 8, 2), (8, 12, 2),
-              (4, 16, 2), (4, 8, 3), (2, 8, 4)]
+CANDIDATES = [(16, 8, 1), (16, 12, 1), (15, 5, 1), (15, 4, 1), (15, 3, 1), (12, 6, 1), (12, 4, 1), (12, 3, 1),
+              (8, 16, 1), (8, 8, 2), (8, 12, 2), (4, 16, 2), (4, 8, 3), (2, 8, 4)]
 _DEFAULT_CACHE = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "_build",
                               "autotune.json")
 _lock = threading.Lock()

@@ -357,7 +357,7 @@ struct MatFixedEncode2Body {
   static constexpr int kGroups = 2;
   static constexpr int kLayout = kLayoutSymbol;
   static constexpr int kMaxOut = M;
-  static constexpr int kMaxWarps = 12;
+  static constexpr int kMaxWarps = 15;
   static constexpr int kMinBlocks = 1;
   static_assert(kind_layout(KIND) == kLayoutSymbol, "symbol-layout kinds only");
   __device__ static bool matches(const TileOp& o) { return o.op == kOpMatEncode && o.m == M && o.k == K; }
@@ -375,9 +375,9 @@ struct PolyDecode2Body {
   static constexpr int kGroups = 2;
   static constexpr int kLayout = kLayoutSymbol;
   static constexpr int kMaxOut = M;
-  // two groups of syndromes and outputs live at once: 12 consumer warps in
-  // one CTA per SM keep them in registers (128 a thread)
-  static constexpr int kMaxWarps = 12;
+  // two groups of syndromes and outputs live at once: up to 15 consumer
+  // warps in one CTA per SM keep them in registers (128 a thread)
+  static constexpr int kMaxWarps = 15;
   static constexpr int kMinBlocks = 1;
   __device__ static bool matches(const TileOp& o) { return o.op == kOpDecode && o.m == M; }
   template <class Tile>
@@ -436,9 +436,9 @@ struct MatFixedDecode2Body {
   static constexpr int kGroups = 2;
   static constexpr int kLayout = kind_layout(KIND);
   static constexpr int kMaxOut = M;
-  // symbol layout: 12 warps at 128 registers; packet layout: a tile's span
-  // (warps x 256 bytes) must divide the packet, so at most 8 warps
-  static constexpr int kMaxWarps = kLayout == kLayoutSymbol ? 12 : 8;
+  // symbol layout: up to 15 warps at 128 registers; packet layout: a
+  // tile's span (warps x 256 bytes) must divide the packet, so at most 8
+  static constexpr int kMaxWarps = kLayout == kLayoutSymbol ? 15 : 8;
   static constexpr int kMinBlocks = 1;
   __device__ static bool matches(const TileOp& o) { return o.op == kOpMatDecode && o.m == M && o.k == K; }
   template <class Tile>
