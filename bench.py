@@ -49,13 +49,13 @@ WORKLOAD = ("RS(10,4) GF(2^8), 1 GiB data in 102 stripes of 10 x 1 MiB blocks; p
 # <op>` (16 stripes, one launch) divided by 16; a bench launch streams 102
 # stripes, so its traffic is 102 x this.  Valid only for the kernel sources
 # with the recorded digest (kernel_digest()); otherwise reported as null.
-TRAFFIC = {"digest": "f17f67ffb4ecf4bb", "per_stripe": {
-    "poly_encode": 12527008,
-    "poly_decode": 12738672,
-    "vandermonde_encode": 12695936,
-    "vandermonde_decode": 12638640,
-    "cauchy_encode": 12581008,
-    "cauchy_decode": 12852960}}
+TRAFFIC = {"digest": "b1292447090f7c2a", "per_stripe": {
+    "poly_encode": 12697408,
+    "poly_decode": 12730848,
+    "vandermonde_encode": 12699456,
+    "vandermonde_decode": 12604784,
+    "cauchy_encode": 12596016,
+    "cauchy_decode": 12761056}}
 
 
 def kernel_digest() -> str:
