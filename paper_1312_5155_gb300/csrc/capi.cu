@@ -172,8 +172,9 @@ rs_status select_kernel(const rs_code* c, int op, int M, PreparedOp& po) {
   }
   po.key = key;
   po.entry = find_kernel(key);
-  // a two-group packet kernel needs tiles of at least 256 bytes per packet
-  // row: smaller packets take the runtime-matrix kernel
+  // a packet kernel's tiles are whole warps of units (G 32-bit words of each
+  // packet row), so packets must hold a multiple of 32 units: packets that
+  // are not a multiple of 256 bytes take the one-group runtime-matrix kernel
   if (po.entry && key.layout == kLayoutPacket && po.entry->groups > 1 &&
       c->packet_bytes % (size_t)(128 * po.entry->groups)) {
     key.family = kFamMatRuntime;
@@ -292,15 +293,8 @@ rs_status prepare_decode(rs_code* c, const int* er, int e, void* const* blocks, 
   return RS_OK;
 }
 
-// Consumer warps for a launch: the tuned value capped by the kernel; in
-// the packet layout a tile spans nc*128*groups bytes of a packet, which
-// must divide every packet size of the launch.
-int pick_warps(const TuneCfg& t, int cap, int groups, int layout, uint32_t packet_gcd) {
-  int nc = std::max(1, std::min(t.consumer_warps, cap));
-  if (layout == kLayoutPacket)
-    while (nc > 1 && packet_gcd % (uint32_t)(nc * 128 * groups)) --nc;
-  return nc;
-}
+// Consumer warps for a launch: the tuned value capped by the kernel.
+int pick_warps(const TuneCfg& t, int cap) { return std::max(1, std::min(t.consumer_warps, cap)); }
 
 LaunchShape make_shape(const TuneCfg& t, int nc, int w, int groups, int num_sms, uint32_t& slice, uint32_t& depth) {
   slice = (uint32_t)(nc * groups) * segment_bytes(w);
@@ -324,7 +318,7 @@ rs_status launch_single(rs_code* c, PreparedOp& po, void* stream) {
   if (s != RS_OK) return s;
   JobParams* p = new (std::nothrow) JobParams();
   if (!p) return fail(RS_ENOMEM, "host allocation failed");
-  const int nc = pick_warps(c->tune, po.entry->max_warps, po.entry->groups, po.key.layout, po.d.packet_bytes);
+  const int nc = pick_warps(c->tune, po.entry->max_warps);
   uint32_t slice, depth;
   LaunchShape sh = make_shape(c->tune, nc, c->w, po.entry->groups, c->num_sms, slice, depth);
   p->status = c->d_status;
@@ -685,15 +679,8 @@ rs_status rs_batch_set(rs_batch* b, const rs_op* ops, int n_ops, void* stream) {
     rs_batch::Group gr{};
     gr.entry = group_entry[g];
     const int layout = prep[members[g][0]].key.layout;
-    uint32_t pg = 0;
-    for (int i : members[g]) {
-      const uint32_t pb = prep[i].d.packet_bytes;
-      uint32_t a = pg, c2 = pb;
-      while (c2) { uint32_t t = a % c2; a = c2; c2 = t; }
-      pg = a;
-    }
     gr.layout = layout;
-    gr.nc = pick_warps(b->tune, gr.entry->max_warps, gr.entry->groups, layout, pg);
+    gr.nc = pick_warps(b->tune, gr.entry->max_warps);
     const int w = gr.entry->key.w;
     gr.sh = make_shape(b->tune, gr.nc, w, gr.entry->groups, b->num_sms, gr.slice, gr.depth);
     uint32_t tiles = 0;

@@ -84,13 +84,14 @@ struct JobParams {
 // registers before they release that slot.
 constexpr int kHeaderCoefWords = selector_words(kMaxM, 16);
 struct alignas(16) TileHeader {
-  uint64_t goff;
+  uint64_t goff;            // symbol: byte offset; packet: offset of the first super-packet
   uint64_t read_mask;
   uint64_t pmask;
   uint64_t ptrs;            // this stripe's pointer table (ragged-end reads)
   uint64_t outp[kMaxM];
-  uint32_t len;
-  uint32_t span_off;
+  uint32_t len;             // symbol: bytes; packet: units
+  uint32_t col0;            // packet: first unit's column in its super-packet
+  uint32_t head, whole;     // packet: units of the leading partial super-packet, whole ones after it
   uint32_t packet_bytes;
   uint16_t n_in, n_out;
   uint8_t op, m, k, n_pos, e, pad[3];

@@ -20,12 +20,15 @@
 //     warp-wide load/store covers 512 contiguous bytes.  Slice of one block
 //     per tile = NC segments, one bulk copy.
 //   packet (§2.3 bit-matrix layout): a block is super-packets of W packets of
-//     P bytes; packet c holds bit c of the super-packet's 8P symbols.  A tile
-//     covers a span of NC*128 bytes at the same offset of the W packets of one
-//     super-packet (W bulk copies per block, one when the span is a whole
-//     packet and the W packets are contiguous); lane l of warp v owns 32-bit
-//     word v*32 + l of the span in each packet, which are already the W
-//     bit-planes of 32 symbols.
+//     P bytes; packet c holds bit c of the super-packet's 8P symbols.  A
+//     unit is G adjacent 32-bit words at the same offset of the W packets of
+//     one super-packet (already the W bit-planes of 32G symbols); a block is
+//     a sequence of units, super-packet after super-packet (U = P / 4G per
+//     super-packet).  A tile covers NC*32 consecutive units, lane l of warp v
+//     owning unit v*32 + l: a leading partial super-packet (W bulk copies
+//     per block, one per packet row), whole super-packets (one bulk copy:
+//     they are contiguous) and a trailing partial one (W copies).  The slot
+//     holds the three parts one after the other, each row-major.
 #pragma once
 #include <cuda_runtime.h>
 
@@ -67,28 +70,40 @@ __device__ __forceinline__ uint32_t find_stripe(const StripeDesc* st, uint32_t n
 }
 
 // Where tile `lt` of a stripe lies: symbol layout -> one byte range
-// [goff, goff + len) of every block; packet layout -> super-packet `sp_off`,
-// byte `span_off` inside each packet (len = span).
+// [goff, goff + len) of every block; packet layout -> units
+// [lt*T, lt*T + len) (T = slice / (W*4G) units per tile), starting at column
+// col0 of the super-packet at byte goff: `head` units finish that
+// super-packet (0 when the tile starts on a boundary), `whole` complete
+// super-packets follow, then len - head - whole*U units of the next.
 struct TileGeom {
   uint64_t goff;
   uint32_t len;
-  uint32_t span_off;
+  uint32_t col0;
+  uint32_t head;
+  uint32_t whole;
 };
 
+template <int G>
 __device__ __forceinline__ TileGeom tile_geom(const StripeDesc& d, uint32_t lt, uint32_t slice, int w) {
   TileGeom g;
+  g.col0 = g.head = g.whole = 0;
   if (d.layout == kLayoutSymbol) {
     g.goff = (uint64_t)lt * slice;
     const uint64_t rem = d.bytes - g.goff;
     g.len = rem < slice ? (uint32_t)rem : slice;
-    g.span_off = 0;
   } else {
-    const uint32_t span = slice / (uint32_t)w;
-    const uint32_t per_sp = d.packet_bytes / span;
-    const uint32_t sp = lt / per_sp;
-    g.goff = (uint64_t)sp * (uint64_t)w * d.packet_bytes;
-    g.span_off = (lt - sp * per_sp) * span;
-    g.len = span;
+    const uint32_t ub = 4u * (uint32_t)G;
+    const uint32_t T = slice / ((uint32_t)w * ub);
+    const uint32_t U = d.packet_bytes / ub;
+    const uint64_t total = d.bytes / ((uint64_t)w * ub);
+    const uint64_t u0 = (uint64_t)lt * T;
+    const uint64_t rem = total - u0;
+    g.len = rem < T ? (uint32_t)rem : T;
+    const uint64_t sp = u0 / U;
+    g.goff = sp * (uint64_t)w * d.packet_bytes;
+    g.col0 = (uint32_t)(u0 - sp * U);
+    g.head = g.col0 ? min(U - g.col0, g.len) : 0u;
+    g.whole = (g.len - g.head) / U;
   }
   return g;
 }
@@ -238,21 +253,24 @@ struct SymTile {
   }
 };
 
-// G column groups per lane: lane `word` owns the G adjacent 32-bit words
-// G*word .. G*word+G-1 of every packet row of the span; group g is words
-// g*W .. g*W+W-1 of a load or store (word g of each of the W rows).
+// Packet layout: thread `unit` (warp*32 + lane) owns unit `unit` of the tile
+// (G adjacent 32-bit words of each of the W packet rows); group g of a load
+// or store is words g*W .. g*W+W-1 (word g of each row).  Where the unit
+// lies in the slot and in the block is worked out once per tile.
 template <int W, int MO, int G = 1>
 struct PacketTile {
   static_assert(G == 1 || G == 2, "one or two groups");
+  static constexpr uint32_t kUnitBytes = 4u * G;
   Ring* ring;
   const uint64_t* ptrs;
   uint64_t outp[MO];  // output pointers, loaded at tile start
   int n_in;
-  uint64_t goff;      // super-packet offset
-  uint32_t span_off;  // offset inside each packet
-  uint32_t span;      // bytes per packet row in the slot
-  uint32_t P;         // packet bytes
-  uint32_t word;      // this thread's first 32-bit word group inside the span
+  uint64_t gbase;     // byte offset of this unit's row 0 in a block
+  uint32_t sbase;     // byte offset of this unit's row 0 in a slot
+  uint32_t srow;      // slot bytes between packet rows of this unit
+  uint32_t P;         // packet bytes (block bytes between packet rows)
+  uint32_t unit;      // this thread's unit inside the tile
+  bool valid;         // the unit exists (the last tile of a block may be short)
   int* status;
   unsigned long long limit;
   bool failed;
@@ -260,11 +278,31 @@ struct PacketTile {
   __device__ __forceinline__ void begin(const TileHeader& h) {
     ptrs = reinterpret_cast<const uint64_t*>(h.ptrs);
     n_in = h.n_in;
-    goff = h.goff;
-    span_off = h.span_off;
     P = h.packet_bytes;
 #pragma unroll
     for (int t = 0; t < MO; ++t) outp[t] = h.outp[t];
+    const uint32_t U = P / kUnitBytes, n = h.len, head = h.head, whole = h.whole;
+    const uint32_t sp_bytes = (uint32_t)W * P;
+    valid = unit < n;
+    if (!valid) {  // reads row 0 of the slot, stores nothing
+      sbase = 0;
+      srow = 0;
+      gbase = 0;
+    } else if (unit < head) {  // leading partial super-packet
+      sbase = unit * kUnitBytes;
+      srow = head * kUnitBytes;
+      gbase = h.goff + (uint64_t)(h.col0 + unit) * kUnitBytes;
+    } else if (unit < head + whole * U) {  // whole super-packets: same layout as the block
+      const uint32_t v = unit - head, j = v / U, col = v - j * U;
+      sbase = (uint32_t)W * kUnitBytes * head + j * sp_bytes + col * kUnitBytes;
+      srow = P;
+      gbase = h.goff + (uint64_t)((head ? 1u : 0u) + j) * sp_bytes + (uint64_t)col * kUnitBytes;
+    } else {  // trailing partial super-packet
+      const uint32_t before = head + whole * U, v = unit - before;
+      sbase = (uint32_t)W * kUnitBytes * before + v * kUnitBytes;
+      srow = (n - before) * kUnitBytes;
+      gbase = h.goff + (uint64_t)((head ? 1u : 0u) + whole) * sp_bytes + (uint64_t)v * kUnitBytes;
+    }
   }
 
   __device__ __forceinline__ void load(int i, uint32_t* x) {
@@ -272,15 +310,15 @@ struct PacketTile {
     const uint32_t s = r.s, par = r.par;
     r.advance();
     wait_or_fail(&r.full[s], par, failed, status, kDevErrTimeoutFull, limit);
-    const uint8_t* slot = r.slots + (size_t)s * r.slice;
+    const uint8_t* slot = r.slots + (size_t)s * r.slice + sbase;
     // stale after a timed-out wait; store() then writes nothing
     if constexpr (G == 1) {
 #pragma unroll
-      for (int c = 0; c < W; ++c) x[c] = *reinterpret_cast<const uint32_t*>(slot + (size_t)c * span + 4u * word);
+      for (int c = 0; c < W; ++c) x[c] = *reinterpret_cast<const uint32_t*>(slot + c * srow);
     } else {
 #pragma unroll
       for (int c = 0; c < W; ++c) {
-        const uint2 v = *reinterpret_cast<const uint2*>(slot + (size_t)c * span + 8u * word);
+        const uint2 v = *reinterpret_cast<const uint2*>(slot + c * srow);
         x[c] = v.x;
         x[W + c] = v.y;
       }
@@ -289,8 +327,8 @@ struct PacketTile {
   }
 
   __device__ __forceinline__ void store(int t, const uint32_t* x) {
-    if (failed) return;
-    uint8_t* out = reinterpret_cast<uint8_t*>(select_out(outp, t)) + goff + span_off + 4u * G * word;
+    if (failed || !valid) return;
+    uint8_t* out = reinterpret_cast<uint8_t*>(select_out(outp, t)) + gbase;
     if constexpr (G == 1) {
 #pragma unroll
       for (int c = 0; c < W; ++c) *reinterpret_cast<uint32_t*>(out + (size_t)c * P) = x[c];
@@ -437,9 +475,8 @@ struct MatFixedDecode2Body {
   static constexpr int kGroups = 2;
   static constexpr int kLayout = kind_layout(KIND);
   static constexpr int kMaxOut = M;
-  // symbol layout: up to 15 warps at 128 registers; packet layout: a
-  // tile's span (warps x 256 bytes) must divide the packet, so at most 8
-  static constexpr int kMaxWarps = kLayout == kLayoutSymbol ? 15 : 8;
+  // symbol layout: up to 15 warps at 128 registers; packet layout: 12
+  static constexpr int kMaxWarps = kLayout == kLayoutSymbol ? 15 : 12;
   static constexpr int kMinBlocks = 1;
   __device__ static bool matches(const TileOp& o) { return o.op == kOpMatDecode && o.m == M && o.k == K; }
   template <class Tile>
@@ -497,7 +534,7 @@ __device__ __forceinline__ TileRange cta_tiles(uint32_t total_tiles) {
   return TileRange{b, min(b + per, total_tiles)};
 }
 
-template <int W, int LAYOUT>
+template <int W, int LAYOUT, int G>
 __device__ __forceinline__ void producer_loop(const JobParams& p, const StripeDesc* stripes, const uint64_t* ptrs,
                                               const uint32_t* coef, TileHeader* headers, Ring& ring,
                                               uint32_t n_stripes, uint32_t total_tiles) {
@@ -520,7 +557,7 @@ __device__ __forceinline__ void producer_loop(const JobParams& p, const StripeDe
       next_begin = si + 1 < n_stripes ? stripes[si + 1].tile_begin : total_tiles;
       fresh = true;
     }
-    const TileGeom g = tile_geom(d, tile - d.tile_begin, ring.slice, W);
+    const TileGeom g = tile_geom<G>(d, tile - d.tile_begin, ring.slice, W);
     const uint64_t* ip = ptrs + d.ptr_off;
     for (int i = 0; i < d.n_in; ++i) {
       const uint32_t s = ring.s, par = ring.par;
@@ -534,7 +571,9 @@ __device__ __forceinline__ void producer_loop(const JobParams& p, const StripeDe
         TileHeader& h = headers[s];
         h.goff = g.goff;
         h.len = g.len;
-        h.span_off = g.span_off;
+        h.col0 = g.col0;
+        h.head = g.head;
+        h.whole = g.whole;
         h.read_mask = d.read_mask;
         h.pmask = d.pmask;
         h.ptrs = reinterpret_cast<uint64_t>(ip);
@@ -572,13 +611,30 @@ __device__ __forceinline__ void producer_loop(const JobParams& p, const StripeDe
           mbar_arrive(&ring.full[s]);
         }
       } else {
-        const uint32_t span = ring.slice / (uint32_t)W;
-        mbar_arrive_expect_tx(&ring.full[s], ring.slice);
-        if (span == d.packet_bytes) {  // whole packets: the W rows are contiguous
-          tma_load_1d(dst, src, ring.slice, &ring.full[s]);
-        } else {
+        // head rows, whole super-packets, tail rows (every size a multiple
+        // of 32 units, so of 128 bytes)
+        constexpr uint32_t ub = 4u * (uint32_t)G;
+        const uint32_t P = d.packet_bytes, sp_bytes = (uint32_t)W * P;
+        const uint32_t U = P / ub;
+        const uint32_t tail = g.len - g.head - g.whole * U;
+        mbar_arrive_expect_tx(&ring.full[s], g.len * ub * (uint32_t)W);
+        uint8_t* o = dst;
+        const uint8_t* b = src;
+        if (g.head) {
           for (int c = 0; c < W; ++c)
-            tma_load_1d(dst + (size_t)c * span, src + (size_t)c * d.packet_bytes + g.span_off, span, &ring.full[s]);
+            tma_load_1d(o + (size_t)c * g.head * ub, b + (size_t)c * P + (size_t)g.col0 * ub, g.head * ub,
+                        &ring.full[s]);
+          o += (size_t)W * g.head * ub;
+          b += sp_bytes;
+        }
+        if (g.whole) {
+          tma_load_1d(o, b, g.whole * sp_bytes, &ring.full[s]);
+          o += (size_t)g.whole * sp_bytes;
+          b += (size_t)g.whole * sp_bytes;
+        }
+        if (tail) {
+          for (int c = 0; c < W; ++c)
+            tma_load_1d(o + (size_t)c * tail * ub, b + (size_t)c * P, tail * ub, &ring.full[s]);
         }
       }
       ring.advance();
@@ -625,7 +681,8 @@ __global__ void __launch_bounds__((Body::kMaxWarps + 1) * 32, Body::kMinBlocks)
   const uint32_t total_tiles = p.counts ? p.counts[1] : p.total_tiles;
 
   if (warp == nc) {
-    if (lane == 0) producer_loop<W, Body::kLayout>(p, stripes, ptrs, coef, headers, ring, n_stripes, total_tiles);
+    if (lane == 0)
+      producer_loop<W, Body::kLayout, Body::kGroups>(p, stripes, ptrs, coef, headers, ring, n_stripes, total_tiles);
     return;
   }
 
@@ -640,8 +697,7 @@ __global__ void __launch_bounds__((Body::kMaxWarps + 1) * 32, Body::kMinBlocks)
     tile.lane = (uint32_t)lane;
     tile.seg = (uint32_t)warp * (uint32_t)Body::kGroups * segment_bytes(W);
   } else {
-    tile.word = (uint32_t)(warp * 32 + lane);
-    tile.span = ring.slice / (uint32_t)W;
+    tile.unit = (uint32_t)(warp * 32 + lane);
   }
   const TileRange tr = cta_tiles(total_tiles);
   for (uint32_t t = tr.begin; t < tr.end; ++t) {

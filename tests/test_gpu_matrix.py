@@ -103,3 +103,36 @@ def test_cauchy_block_size_must_fit_packets(rs):
         code.encode(list(t[:10]), list(t[10:]), 16384 + 16)
     with pytest.raises(rs.RSError):
         rs.rs_set_packet_bytes(code.handle, 100)
+
+
+# Packet-layout tiles are runs of consumer_warps x 32 units (G words of each
+# packet row); these shapes make tiles start inside a super-packet, span
+# several, and end short at the block's end.
+@pytest.mark.parametrize("warps", [1, 3, 5, 12, 16])
+@pytest.mark.parametrize("real,w,k,m,pkt,nsp", [("cauchy", 8, 10, 4, 2048, 7), ("cauchy", 8, 10, 4, 256, 37),
+                                                ("cauchy", 8, 10, 4, 768, 5), ("cauchy", 8, 7, 5, 640, 9),
+                                                ("poly_bitmatrix", 8, 10, 4, 1024, 6),
+                                                ("cauchy", 16, 12, 4, 384, 5)])
+def test_packet_tiles_any_warp_count(rs, real, w, k, m, pkt, nsp, warps):
+    import torch
+    B = nsp * w * pkt
+    code = rs.Code(k, m, w, real, packet_bytes=pkt)
+    code.set_launch(warps, 4, 1)
+    host = stripe(w, k, m, B, seed=11)
+    ref = host.copy()
+    O.encode(real, w, k, m, ref, packet_bytes=pkt)
+    buf, rows = device_blocks(host)
+    buf[k:] = 0x5A
+    code.encode(rows[:k], rows[k:], B)
+    torch.cuda.synchronize()
+    assert np.array_equal(to_host(buf, B), ref)
+    n = k + m
+    for s in range(3):
+        er = inputs.erasure_pattern(inputs.config_seed(3), s, n, m - s % 2)
+        bad = ref.copy()
+        bad[er] = 0xC3
+        buf, rows = device_blocks(bad)
+        code.decode(er, rows, B)
+        torch.cuda.synchronize()
+        assert np.array_equal(to_host(buf, B), ref), er
+    assert code.poll_status() == 0
