@@ -296,14 +296,51 @@ rs_status prepare_decode(rs_code* c, const int* er, int e, void* const* blocks, 
 // Consumer warps for a launch: the tuned value capped by the kernel.
 int pick_warps(const TuneCfg& t, int cap) { return std::max(1, std::min(t.consumer_warps, cap)); }
 
-LaunchShape make_shape(const TuneCfg& t, int nc, int w, int groups, int num_sms, uint32_t& slice, uint32_t& depth) {
+// Bytes of the whole super-packets one packet tile can touch: a tile of T
+// units starts at a multiple of gcd(T, U) inside a super-packet of U units.
+uint32_t packet_whole_bytes(uint32_t slice, int w, int groups, uint32_t packet_bytes) {
+  const uint32_t ub = 4u * (uint32_t)groups;
+  const uint32_t T = slice / ((uint32_t)w * ub), U = packet_bytes / ub;
+  uint32_t a = T, b = U;
+  while (b) {
+    const uint32_t r = a % b;
+    a = b;
+    b = r;
+  }
+  const uint64_t touched = (uint64_t)(U - a + T - 1u) / U + 1u;
+  return (uint32_t)std::min<uint64_t>(touched * (uint64_t)w * packet_bytes, 0xFFFFFFFFull);
+}
+
+// A launch's geometry.  slice = one block's bytes of a tile; slot = the
+// ring's slot stride.  Packet tiles copy the whole super-packets they touch
+// (one bulk copy per block instead of one per packet row of a partial
+// super-packet) when those take at most 3/2 of the tile's own bytes;
+// `whole` reports that choice.
+LaunchShape make_shape(const TuneCfg& t, int nc, int w, int groups, int num_sms, int layout,
+                       const std::vector<uint32_t>& packets, uint32_t& slice, uint32_t& slot, uint32_t& depth,
+                       uint32_t& whole) {
   slice = (uint32_t)(nc * groups) * segment_bytes(w);
+  slot = slice;
+  whole = 0;
+  if (layout == kLayoutPacket && !packets.empty()) {
+    uint32_t need = slice;
+    bool fits = true;
+    for (uint32_t pb : packets) {
+      const uint32_t wb = packet_whole_bytes(slice, w, groups, pb);
+      fits = fits && 2ull * wb <= 3ull * slice;
+      need = std::max(need, wb);
+    }
+    if (fits) {
+      whole = 1;
+      slot = need;
+    }
+  }
   depth = (uint32_t)std::max(2, t.depth);
   const size_t budget = kMaxDynamicSmem / (size_t)std::max(1, t.ctas_per_sm);
-  while (depth > 2 && ring_smem_bytes(depth, slice) > budget) --depth;
+  while (depth > 2 && ring_smem_bytes(depth, slot) > budget) --depth;
   LaunchShape sh;
   sh.threads = (nc + 1) * 32;
-  sh.smem = ring_smem_bytes(depth, slice);
+  sh.smem = ring_smem_bytes(depth, slot);
   sh.grid = std::max(1, num_sms * std::max(1, t.ctas_per_sm));
   return sh;
 }
@@ -319,11 +356,14 @@ rs_status launch_single(rs_code* c, PreparedOp& po, void* stream) {
   JobParams* p = new (std::nothrow) JobParams();
   if (!p) return fail(RS_ENOMEM, "host allocation failed");
   const int nc = pick_warps(c->tune, po.entry->max_warps);
-  uint32_t slice, depth;
-  LaunchShape sh = make_shape(c->tune, nc, c->w, po.entry->groups, c->num_sms, slice, depth);
+  uint32_t slice, slot, depth, whole;
+  LaunchShape sh = make_shape(c->tune, nc, c->w, po.entry->groups, c->num_sms, po.key.layout, {po.d.packet_bytes},
+                              slice, slot, depth, whole);
   p->status = c->d_status;
   p->n_stripes = 1;
   p->slice_bytes = slice;
+  p->slot_bytes = slot;
+  p->packet_whole = whole;
   p->depth = depth;
   p->wait_limit_ns = c->wait_limit_ns;
   p->inject = c->inject_next;
@@ -363,7 +403,7 @@ struct rs_batch {
     const KernelEntry* entry;
     int layout;
     int nc;
-    uint32_t slice, depth;
+    uint32_t slice, slot, depth, whole;
     uint32_t n_stripes, tiles;
     LaunchShape sh;
   };
@@ -682,7 +722,11 @@ rs_status rs_batch_set(rs_batch* b, const rs_op* ops, int n_ops, void* stream) {
     gr.layout = layout;
     gr.nc = pick_warps(b->tune, gr.entry->max_warps);
     const int w = gr.entry->key.w;
-    gr.sh = make_shape(b->tune, gr.nc, w, gr.entry->groups, b->num_sms, gr.slice, gr.depth);
+    std::vector<uint32_t> packets;
+    if (layout == kLayoutPacket)
+      for (int i : members[g]) packets.push_back(prep[i].d.packet_bytes);
+    gr.sh = make_shape(b->tune, gr.nc, w, gr.entry->groups, b->num_sms, layout, packets, gr.slice, gr.slot, gr.depth,
+                       gr.whole);
     uint32_t tiles = 0;
     StripeDesc* region = hs + g * (size_t)b->max_ops;
     for (size_t q = 0; q < members[g].size(); ++q) {
@@ -738,6 +782,8 @@ rs_status rs_batch_launch(rs_batch* b, void* stream) {
     p->n_stripes = gr.n_stripes;
     p->total_tiles = gr.tiles;
     p->slice_bytes = gr.slice;
+    p->slot_bytes = gr.slot;
+    p->packet_whole = gr.whole;
     p->depth = gr.depth;
     cudaError_t e = gr.entry->launch(*p, gr.sh, (cudaStream_t)stream);
     if (e != cudaSuccess) {

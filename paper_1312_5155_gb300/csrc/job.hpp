@@ -71,7 +71,9 @@ struct JobParams {
   uint32_t depth;             // ring slots
   unsigned long long wait_limit_ns;  // bound of every pipeline wait (0 = default 2 s)
   uint32_t inject;            // test hook: kInjectProducerStall
-  uint32_t pad_inject;
+  uint32_t packet_whole;      // packet layout: copy the whole super-packets a tile touches
+  uint32_t slot_bytes;        // ring slot stride (>= slice_bytes; 0 = slice_bytes)
+  uint32_t pad_slot;
   // one stripe passed by value (single-stripe calls need no device tables)
   StripeDesc inl_stripe;
   uint64_t inl_ptrs[kMaxPtrs];

@@ -48,7 +48,8 @@ struct Ring {
   uint64_t* empty;
   uint8_t* slots;
   uint32_t depth;
-  uint32_t slice;
+  uint32_t slice;    // bytes of one block per tile (symbol layout)
+  uint32_t stride;   // bytes between slots (>= slice)
   uint32_t s = 0;    // next slot
   uint32_t par = 0;  // parity of the next slot's current round
   __device__ __forceinline__ void advance() {
@@ -200,7 +201,7 @@ struct SymTile {
     wait_or_fail(&r.full[s], par, failed, status, kDevErrTimeoutFull, limit);
     // After a timed-out wait the slot may hold stale bytes; they are read
     // anyway (the addresses are valid) and store() writes nothing.
-    const uint8_t* slot = r.slots + (size_t)s * r.slice;
+    const uint8_t* slot = r.slots + (size_t)s * r.stride;
     if (whole) {
 #pragma unroll
       for (int c = 0; c < G * W / 4; ++c) {
@@ -271,6 +272,7 @@ struct PacketTile {
   uint32_t P;         // packet bytes (block bytes between packet rows)
   uint32_t unit;      // this thread's unit inside the tile
   bool valid;         // the unit exists (the last tile of a block may be short)
+  bool whole_sp;      // the slot holds whole super-packets (JobParams::packet_whole)
   int* status;
   unsigned long long limit;
   bool failed;
@@ -288,6 +290,11 @@ struct PacketTile {
       sbase = 0;
       srow = 0;
       gbase = 0;
+    } else if (whole_sp) {  // slot = the super-packets from the one at goff on
+      const uint32_t g = h.col0 + unit, j = g / U, col = g - j * U;
+      sbase = j * sp_bytes + col * kUnitBytes;
+      srow = P;
+      gbase = h.goff + (uint64_t)j * sp_bytes + (uint64_t)col * kUnitBytes;
     } else if (unit < head) {  // leading partial super-packet
       sbase = unit * kUnitBytes;
       srow = head * kUnitBytes;
@@ -310,7 +317,7 @@ struct PacketTile {
     const uint32_t s = r.s, par = r.par;
     r.advance();
     wait_or_fail(&r.full[s], par, failed, status, kDevErrTimeoutFull, limit);
-    const uint8_t* slot = r.slots + (size_t)s * r.slice + sbase;
+    const uint8_t* slot = r.slots + (size_t)s * r.stride + sbase;
     // stale after a timed-out wait; store() then writes nothing
     if constexpr (G == 1) {
 #pragma unroll
@@ -600,7 +607,7 @@ __device__ __forceinline__ void producer_loop(const JobParams& p, const StripeDe
         }
         prev_h = s;
       }
-      uint8_t* dst = ring.slots + (size_t)s * ring.slice;
+      uint8_t* dst = ring.slots + (size_t)s * ring.stride;
       const uint8_t* src = reinterpret_cast<const uint8_t*>(ip[i]) + g.goff;
       if constexpr (LAYOUT == kLayoutSymbol) {
         const uint32_t len16 = g.len & ~15u;
@@ -610,6 +617,13 @@ __device__ __forceinline__ void producer_loop(const JobParams& p, const StripeDe
         } else {
           mbar_arrive(&ring.full[s]);
         }
+      } else if (p.packet_whole) {
+        // every super-packet the tile touches, in one copy
+        const uint32_t sp_bytes = (uint32_t)W * d.packet_bytes;
+        const uint32_t U = d.packet_bytes / (4u * (uint32_t)G);
+        const uint32_t bytes = ((g.col0 + g.len - 1u) / U + 1u) * sp_bytes;
+        mbar_arrive_expect_tx(&ring.full[s], bytes);
+        tma_load_1d(dst, src, bytes, &ring.full[s]);
       } else {
         // head rows, whole super-packets, tail rows (every size a multiple
         // of 32 units, so of 128 bytes)
@@ -664,6 +678,7 @@ __global__ void __launch_bounds__((Body::kMaxWarps + 1) * 32, Body::kMinBlocks)
   ring.slots = reinterpret_cast<uint8_t*>(headers) + (size_t)depth * kHeaderBytes;
   ring.depth = depth;
   ring.slice = p.slice_bytes;
+  ring.stride = p.slot_bytes ? p.slot_bytes : p.slice_bytes;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int nc = (int)(blockDim.x >> 5) - 1;
   if (threadIdx.x == 0) {
@@ -698,6 +713,7 @@ __global__ void __launch_bounds__((Body::kMaxWarps + 1) * 32, Body::kMinBlocks)
     tile.seg = (uint32_t)warp * (uint32_t)Body::kGroups * segment_bytes(W);
   } else {
     tile.unit = (uint32_t)(warp * 32 + lane);
+    tile.whole_sp = p.packet_whole != 0;
   }
   const TileRange tr = cta_tiles(total_tiles);
   for (uint32_t t = tr.begin; t < tr.end; ++t) {
