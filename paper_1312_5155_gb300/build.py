@@ -65,9 +65,12 @@ def instances():
             layout = 1 if kind in (2, 4) else 0
             # GF(2^8) codes with m <= 4: two column groups per lane (measured
             # faster for these decodes in both layouts and for the
-            # symbol-layout encodes; the LFSR encode keeps one)
-            two = op == 3 and w == 8 and m <= 4
-            two_enc = op == 2 and layout == 0 and w == 8 and m <= 4
+            # symbol-layout encodes; the LFSR encode keeps one).  In the
+            # symbol layout only up to k = 12: the unrolled per-input code of
+            # two groups at k = 20 overflows the instruction cache (encode
+            # 4175 -> 2747 GB/s)
+            two = op == 3 and w == 8 and m <= 4 and (layout == 1 or k <= 12)
+            two_enc = op == 2 and layout == 0 and w == 8 and m <= 4 and k <= 12
             body = (f"MatFixedDecode2Body<{w}, {k}, {m}, {kind}>" if two else
                     f"MatFixedEncode2Body<{w}, {k}, {m}, {kind}>" if two_enc else f"MatFixedBody<{w}, {k}, {m}, {kind}, {op}>")
             out.append((f"matfix_w{w}_k{k}_m{m}_kind{kind}_op{op}", body,
