@@ -45,13 +45,17 @@ M_RANGE = {8: range(1, 9), 16: range(1, 5)}
 
 
 def instances():
+    """(name, body, key) of every compiled kernel.  Keys with wide=1 are the
+    two-column-group variants of a one-group kernel with the same key; the
+    library picks them for large blocks (see select_kernel in capi.cu)."""
     out = []
     for w in (8, 16):
         for m in M_RANGE[w]:
             for op in (0, 1):
-                # GF(2^8) decodes with M <= 4: two column groups per lane
-                body = f"PolyDecode2Body<{w}, {m}>" if (op == 1 and w == 8 and m <= 4) else f"PolyBody<{w}, {m}, {op}>"
-                out.append((f"poly_w{w}_m{m}_op{op}", body, dict(family=0, w=w, m=m, op=op)))
+                key = dict(family=0, w=w, m=m, op=op)
+                out.append((f"poly_w{w}_m{m}_op{op}", f"PolyBody<{w}, {m}, {op}>", key))
+                if op == 1 and w == 8 and m <= 4:
+                    out.append((f"poly_w{w}_m{m}_op{op}_g2", f"PolyDecode2Body<{w}, {m}>", dict(key, wide=1)))
     for w in (8, 16):
         for m in M_RANGE[w]:
             for op in (2, 3):
@@ -63,18 +67,19 @@ def instances():
     for (w, k, m), kind in fixed:
         for op in (2, 3):
             layout = 1 if kind in (2, 4) else 0
-            # GF(2^8) codes with m <= 4: two column groups per lane (measured
-            # faster for these decodes in both layouts and for the
-            # symbol-layout encodes; the LFSR encode keeps one).  In the
-            # symbol layout only up to k = 12: the unrolled per-input code of
-            # two groups at k = 20 overflows the instruction cache (encode
-            # 4175 -> 2747 GB/s)
-            two = op == 3 and w == 8 and m <= 4 and (layout == 1 or k <= 12)
-            two_enc = op == 2 and layout == 0 and w == 8 and m <= 4 and k <= 12
-            body = (f"MatFixedDecode2Body<{w}, {k}, {m}, {kind}>" if two else
-                    f"MatFixedEncode2Body<{w}, {k}, {m}, {kind}>" if two_enc else f"MatFixedBody<{w}, {k}, {m}, {kind}, {op}>")
-            out.append((f"matfix_w{w}_k{k}_m{m}_kind{kind}_op{op}", body,
-                        dict(family=2, w=w, m=m, op=op, layout=layout, kind=kind, k=k)))
+            name = f"matfix_w{w}_k{k}_m{m}_kind{kind}_op{op}"
+            key = dict(family=2, w=w, m=m, op=op, layout=layout, kind=kind, k=k)
+            out.append((name, f"MatFixedBody<{w}, {k}, {m}, {kind}, {op}>", key))
+            # GF(2^8) codes with m <= 4 also get two column groups per lane
+            # (decodes in both layouts, symbol-layout encodes; the LFSR encode
+            # keeps one).  In the symbol layout only up to k = 12: the unrolled
+            # per-input code of two groups at k = 20 overflows the
+            # instruction cache (encode 4175 -> 2747 GB/s).
+            if w == 8 and m <= 4 and (layout == 1 or k <= 12):
+                if op == 3:
+                    out.append((name + "_g2", f"MatFixedDecode2Body<{w}, {k}, {m}, {kind}>", dict(key, wide=1)))
+                elif layout == 0:
+                    out.append((name + "_g2", f"MatFixedEncode2Body<{w}, {k}, {m}, {kind}>", dict(key, wide=1)))
     for (w, ms) in MIXED_POLY:
         bodies = ", ".join(f"PolyBody<{w}, {m}, {op}>" for m in ms for op in (0, 1))
         mset = sum(1 << m for m in ms)
@@ -128,11 +133,11 @@ def generate_units() -> list[str]:
     lines.append("static const KernelEntry* build_table() {")
     lines.append(f"  static KernelEntry t[{len(insts)}];")
     for i, (name, _, key) in enumerate(insts):
-        k = dict(family=0, w=0, m=0, op=0, layout=0, kind=0, k=0, mset=0)
+        k = dict(family=0, w=0, m=0, op=0, layout=0, kind=0, k=0, mset=0, wide=0)
         k.update(key)
         lines.append(f"  t[{i}] = KernelEntry{{KernelKey{{{k['family']}, {k['w']}, {k['m']}, {k['op']}, "
-                     f"{k['layout']}, {k['kind']}, {k['k']}, {k['mset']}u}}, launch_{name}, warps_{name}(), groups_{name}(), "
-                     f'"{name}"}};')
+                     f"{k['layout']}, {k['kind']}, {k['k']}, {k['mset']}u, {k['wide']}}}, launch_{name}, "
+                     f'warps_{name}(), groups_{name}(), "{name}"}};')
     lines.append("  return t;\n}")
     lines.append("const KernelEntry* const kKernelRegistryPtr = build_table();")
     lines.append(f"const int kKernelRegistrySize = {len(insts)};")

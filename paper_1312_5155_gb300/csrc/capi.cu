@@ -152,7 +152,13 @@ struct PreparedOp {
   bool noop = false;
 };
 
-rs_status select_kernel(const rs_code* c, int op, int M, PreparedOp& po) {
+// Two-column-group kernels (KernelKey::wide) cover twice the columns per
+// tile; below these block sizes the coarser tiles leave warps idle on the
+// ragged last tile of every block and the one-group kernel measured faster.
+constexpr size_t kWideSymbolMinBytes = 256u << 10;
+constexpr size_t kWidePacketMinBytes = 8u << 10;
+
+rs_status select_kernel(const rs_code* c, int op, int M, size_t B, PreparedOp& po) {
   KernelKey key;
   key.w = c->w;
   key.m = M;
@@ -170,19 +176,18 @@ rs_status select_kernel(const rs_code* c, int op, int M, PreparedOp& po) {
       key.family = kFamMatRuntime;
     }
   }
-  po.key = key;
-  po.entry = find_kernel(key);
-  // a packet kernel's tiles are whole warps of units (G 32-bit words of each
-  // packet row), so packets must hold a multiple of 32 units: packets that
-  // are not a multiple of 256 bytes take the one-group runtime-matrix kernel
-  if (po.entry && key.layout == kLayoutPacket && po.entry->groups > 1 &&
-      c->packet_bytes % (size_t)(128 * po.entry->groups)) {
-    key.family = kFamMatRuntime;
-    key.kind = 0;
-    key.k = 0;
-    po.key = key;
+  po.entry = nullptr;
+  if (B >= (key.layout == kLayoutPacket ? kWidePacketMinBytes : kWideSymbolMinBytes)) {
+    key.wide = 1;
     po.entry = find_kernel(key);
+    // a packet kernel's tiles are whole warps of units (G 32-bit words of
+    // each packet row), so its packets must hold a multiple of 32 units
+    if (po.entry && key.layout == kLayoutPacket && c->packet_bytes % (size_t)(128 * po.entry->groups))
+      po.entry = nullptr;
+    if (!po.entry) key.wide = 0;
   }
+  if (!po.entry) po.entry = find_kernel(key);
+  po.key = key;
   if (!po.entry) return fail(RS_EUNSUPPORTED, "no kernel compiled for this code");
   return RS_OK;
 }
@@ -202,7 +207,7 @@ rs_status prepare_encode(rs_code* c, const void* const* data, void* const* parit
   for (int j = 0; j < c->m; ++j) all.push_back(parity[j]);
   rs_status s = check_blocks(c, all, B);
   if (s != RS_OK) return s;
-  if ((s = select_kernel(c, kOpEncode, c->m, po)) != RS_OK) return s;
+  if ((s = select_kernel(c, kOpEncode, c->m, B, po)) != RS_OK) return s;
   po.noop = B == 0;
   StripeDesc& d = po.d;
   fill_common(c, B, d);
@@ -275,7 +280,7 @@ rs_status prepare_decode(rs_code* c, const int* er, int e, void* const* blocks, 
   if ((s = get_plan(c, er, e, pl)) != RS_OK) return s;
   po.noop = e == 0 || B == 0;
   if (e == 0) return RS_OK;
-  if ((s = select_kernel(c, kOpDecode, pl.M, po)) != RS_OK) return s;
+  if ((s = select_kernel(c, kOpDecode, pl.M, B, po)) != RS_OK) return s;
   StripeDesc& d = po.d;
   fill_common(c, B, d);
   d.read_mask = pl.read_mask;

@@ -26,6 +26,7 @@ struct KernelKey {
   int kind = 0;    // kKindVandermonde / kKindCauchy for kFamMatFixed
   int k = 0;       // data blocks for kFamMatFixed
   uint32_t mset = 0;  // kFamPolyMixed: bit M set for every M covered
+  int wide = 0;       // 1: the two-column-group variant of the same kernel
 };
 
 using Launcher = cudaError_t (*)(const JobParams&, const LaunchShape&, cudaStream_t);
@@ -43,7 +44,7 @@ extern const int kKernelRegistrySize;
 
 inline bool same_key(const KernelKey& a, const KernelKey& b) {
   return a.family == b.family && a.w == b.w && a.m == b.m && a.op == b.op && a.layout == b.layout &&
-         a.kind == b.kind && a.k == b.k && a.mset == b.mset;
+         a.kind == b.kind && a.k == b.k && a.mset == b.mset && a.wide == b.wide;
 }
 
 inline const KernelEntry* find_kernel(const KernelKey& k) {

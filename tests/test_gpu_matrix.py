@@ -33,12 +33,14 @@ CASES = [
     ("vandermonde", 8, 10, 4, 1 << 20, None), ("vandermonde", 8, 10, 4, 65536 + 37, None),
     ("vandermonde", 8, 6, 3, 300000, None), ("vandermonde", 16, 12, 4, 100002, None),
     ("vandermonde", 8, 20, 4, 8192, None), ("vandermonde", 8, 7, 5, 50000, None),
-    ("vandermonde", 16, 5, 3, 4096 + 2, None),
+    ("vandermonde", 16, 5, 3, 4096 + 2, None), ("vandermonde", 8, 10, 4, (1 << 18) + 37, None),
+    ("vandermonde", 8, 12, 4, (1 << 18) + 4000, None), ("poly_matrix", 8, 10, 4, (1 << 18) + 5, None),
     ("cauchy", 8, 10, 4, 8 * 2048 * 8, 2048), ("cauchy", 8, 6, 3, 8 * 2048 * 3, 2048),
     ("cauchy", 16, 12, 4, 16 * 2048 * 2, 2048), ("cauchy", 8, 10, 4, 8 * 512 * 5, 512),
     ("cauchy", 8, 7, 5, 8 * 1024 * 3, 1024), ("cauchy", 16, 3, 2, 16 * 128 * 4, 128),
     ("cauchy", 8, 20, 4, 8 * 384 * 2, 384), ("cauchy", 8, 10, 4, 8 * 128 * 3, 128),
     ("cauchy", 8, 10, 4, 8 * 768 * 2, 768), ("poly_bitmatrix", 8, 10, 4, 8 * 640 * 2, 640),
+    ("cauchy", 8, 10, 4, 8 * 512, 512), ("poly_bitmatrix", 8, 10, 4, 8 * 256 * 3, 256),
     ("poly_matrix", 8, 10, 4, 1 << 20, None), ("poly_matrix", 8, 10, 4, 65536 + 37, None),
     ("poly_matrix", 16, 12, 4, 100002, None), ("poly_matrix", 8, 7, 5, 50000, None),
     ("poly_bitmatrix", 8, 10, 4, 8 * 2048 * 8, 2048), ("poly_bitmatrix", 8, 6, 3, 8 * 1024 * 3, 1024),
