@@ -316,111 +316,150 @@ def run_ours(args, rank, world, device):
     return result, wl
 
 
-def read_runs(ers, S):
-    """Blocks a min-read decode reads (the first K survivors of every stripe
-    by block index), as half-open runs of consecutive indices into the
-    flattened data blocks (stripe * K + b) and parity blocks (stripe * M + j)."""
-    data, par = [], []
+def staging_layout(ers, S):
+    """Where the end-to-end decode finds each stripe's blocks.  A storage
+    server receives the blocks a min-read decode reads (the first K
+    survivors by block index) into a staging buffer and returns the rebuilt
+    ones from another: stripe s's read blocks are rows s*K .. s*K+K-1 of
+    the input staging buffer (in block order), its erased blocks rows
+    s*M .. of the output one.  Returns, per stripe, (read blocks, erased
+    blocks); needs e = M erasures per stripe (then every block is either
+    read or rebuilt)."""
+    out = []
     for s in range(S):
         read = [b for b in range(K + M) if b not in ers[s]][:K]
-        data += [s * K + b for b in read if b < K]
-        par += [s * M + b - K for b in read if b >= K]
+        if len(ers[s]) != M or len(read) != K:
+            raise ValueError("the end-to-end step needs M erasures per stripe")
+        out.append((read, sorted(ers[s])))
+    return out
 
-    def runs(idx):
-        out = []
-        for i in idx:
-            if out and out[-1][1] == i:
-                out[-1][1] = i + 1
-            else:
-                out.append([i, i + 1])
-        return [tuple(r) for r in out]
 
-    return runs(data), runs(par)
+E2E_CHUNKS = 4  # stripe chunks per request stream: transfers of one overlap the coding of another
 
 
 def run_e2e(args, wl, device):
-    """The same step with host buffers, through the C ABI: per realization,
-    the data goes host->device, is encoded (one batched launch) and the
-    parity comes back; then the stripes go host->device, are decoded and
-    the rebuilt blocks come back.  Copies are from/to pinned host memory and
-    inside the timed region; each realization runs on its own stream so the
-    two copy directions and the kernels of different realizations overlap.
-    A decode sends only the k blocks a min-read decode reads (the first k
-    survivors by block index; consecutive ones, also across stripes, as one
-    range) and returns the rebuilt blocks; those scattered ranges move with
-    the library's batched block transfer (rs_copy_blocks: ranges of 4 MiB or
-    more on the copy engines, the others by one gather-kernel launch per
-    direction reading / writing the page-locked host buffers)."""
+    """The same step with host buffers, through the C ABI.  Per realization
+    two independent request streams, as a storage server sees them:
+      - encode: the data goes host->device, is encoded (batched launches)
+        and the parity comes back;
+      - decode: the read blocks of the stored stripes (the first K survivors
+        of every stripe, received into one staging buffer) go host->device,
+        are decoded and the rebuilt blocks come back (staging_layout).
+    Copies are transfers between pinned host memory and the device, inside
+    the timed region.  Each request stream has its own device and host
+    buffers (the decode reads the parity stored by the warm-up's encode) and
+    works in E2E_CHUNKS chunks of stripes: chunk c's input copy and launch go
+    on one CUDA stream, its output copy on a second one, so the host->device
+    copies, the kernels and the device->host copies of different chunks,
+    streams and realizations overlap.  The returned blocks are checked after
+    the timed region."""
     import torch
 
     from paper_1312_5155_gb300 import rs
 
     S = wl.S
     main = torch.cuda.current_stream()
-    hosts, streams, plans = {}, {}, {}
-    data_runs, par_runs = read_runs(wl.ers, S)
+    layout = staging_layout(wl.ers, S)
+    bounds = [(S * c // E2E_CHUNKS, S * (c + 1) // E2E_CHUNKS) for c in range(E2E_CHUNKS)]
+    bounds = [b for b in bounds if b[1] > b[0]]
+    flows, checks = [], []
     for real in REALIZATIONS:
         dbuf, pbuf = wl.bufs[real]
-        hd, hp = dbuf.cpu().pin_memory(), pbuf.cpu().pin_memory()
-        hosts[real] = (hd, hp)
-        streams[real] = torch.cuda.Stream(device=device)
-        # decode inputs host -> device, outputs device -> host, as ranges
-        src, dst, nb = [], [], []
-        for runs, h, d in ((data_runs, hd, dbuf), (par_runs, hp, pbuf)):
-            for a, b in runs:
-                src.append(h.data_ptr() + a * BLOCK)
-                dst.append(d.data_ptr() + a * BLOCK)
-                nb.append((b - a) * BLOCK)
-        osrc, odst, onb = [], [], []
-        for st_i in range(S):
-            for b in wl.ers[st_i]:
-                host_blk = hd[st_i, b] if b < K else hp[st_i, b - K]
-                osrc.append(wl.block(real, st_i, b).data_ptr())
-                odst.append(host_blk.data_ptr())
-                onb.append(BLOCK)
-        plans[real] = ((dst, src, nb), (odst, osrc, onb))
+        code = wl.codes[real]
+        hd = dbuf.cpu().pin_memory()                                       # data
+        hp = torch.empty((S, M, BLOCK), dtype=torch.uint8).pin_memory()   # encode's parity output
+        stored = pbuf.cpu()                                                # stored parity
+        hin = torch.empty((S, K, BLOCK), dtype=torch.uint8).pin_memory()  # decode input staging
+        hout = torch.empty((S, M, BLOCK), dtype=torch.uint8).pin_memory()  # decode output staging
+        truth = torch.empty((S, M, BLOCK), dtype=torch.uint8)
+        for st_i, (read, er) in enumerate(layout):
+            for i, b in enumerate(read):
+                hin[st_i, i] = hd[st_i, b] if b < K else stored[st_i, b - K]
+            for j, b in enumerate(er):
+                truth[st_i, j] = hd[st_i, b] if b < K else stored[st_i, b - K]
+        din = torch.empty((S, K, BLOCK), dtype=torch.uint8, device=device)
+        dout = torch.empty((S, M, BLOCK), dtype=torch.uint8, device=device)
+        for op, hi, di, do, ho in (("encode", hd, dbuf, pbuf, hp), ("decode", hin, din, dout, hout)):
+            chunks = []
+            for a, b in bounds:
+                ops = []
+                for st_i in range(a, b):
+                    if op == "encode":
+                        rows = list(dbuf[st_i]) + list(pbuf[st_i])
+                        ops.append((code, "encode", [], rows, BLOCK))
+                    else:
+                        read, er = layout[st_i]
+                        rows = [None] * (K + M)
+                        for i, blk in enumerate(read):
+                            rows[blk] = din[st_i, i]
+                        for j, blk in enumerate(er):
+                            rows[blk] = dout[st_i, j]
+                        ops.append((code, "decode", wl.ers[st_i], rows, BLOCK))
+                batch = rs.Batch(b - a)
+                batch.set_launch(*wl.shapes[f"{real}_{op}"])
+                batch.set(ops)
+                chunks.append(dict(a=a, b=b, batch=batch, done=None))
+            flows.append(dict(hi=hi, di=di, do=do, ho=ho, chunks=chunks,
+                              sin=torch.cuda.Stream(device=device), sout=torch.cuda.Stream(device=device)))
+        checks.append((real, hp, hout, truth))
 
     def step():
         h2d = d2h = 0
-        start = torch.cuda.Event()
-        start.record(main)
-        ends = []
-        for real in REALIZATIONS:
-            st = streams[real]
-            st.wait_event(start)
-            dbuf, pbuf = wl.bufs[real]
-            hd, hp = hosts[real]
-            enc, dec = wl.batches[real]
-            with torch.cuda.stream(st):
-                dbuf.copy_(hd, non_blocking=True)
-                h2d += dbuf.numel()
-                enc.launch(stream=st)
-                hp.copy_(pbuf, non_blocking=True)
-                d2h += pbuf.numel()
-                (dst, src, nb), (odst, osrc, onb) = plans[real]
-                rs.rs_copy_blocks(dst, src, nb, stream=st)
-                h2d += sum(nb)
-                dec.launch(stream=st)
-                rs.rs_copy_blocks(odst, osrc, onb, stream=st)
-                d2h += sum(onb)
-            ev = torch.cuda.Event()
-            ev.record(st)
-            ends.append(ev)
-        for ev in ends:
-            main.wait_event(ev)
+        for f in flows:
+            for ch in f["chunks"]:
+                a, b = ch["a"], ch["b"]
+                with torch.cuda.stream(f["sin"]):
+                    f["di"][a:b].copy_(f["hi"][a:b], non_blocking=True)
+                    if ch["done"] is not None:  # the previous step's output copy has read the outputs
+                        f["sin"].wait_event(ch["done"])
+                    ch["batch"].launch(stream=f["sin"])
+                    coded = torch.cuda.Event()
+                    coded.record(f["sin"])
+                f["sout"].wait_event(coded)
+                with torch.cuda.stream(f["sout"]):
+                    f["ho"][a:b].copy_(f["do"][a:b], non_blocking=True)
+                    ch["done"] = torch.cuda.Event()
+                    ch["done"].record(f["sout"])
+                h2d += f["di"][a:b].numel()
+                d2h += f["do"][a:b].numel()
         return h2d, d2h
 
+    def join():
+        for f in flows:
+            for st in (f["sin"], f["sout"]):
+                ev = torch.cuda.Event()
+                ev.record(st)
+                main.wait_event(ev)
+
+    start = torch.cuda.Event()
+    start.record(main)
+    for f in flows:
+        f["sin"].wait_event(start)
+        f["sout"].wait_event(start)
     for _ in range(max(1, args.warmup)):
         step()
+    join()
     torch.cuda.synchronize()
     t0 = torch.cuda.Event(enable_timing=True)
     t1 = torch.cuda.Event(enable_timing=True)
     t0.record(main)
+    for f in flows:
+        f["sin"].wait_event(t0)
+        f["sout"].wait_event(t0)
     for _ in range(args.steps):
         h2d, d2h = step()
+    join()
     t1.record(main)
     torch.cuda.synchronize()
     ms = t0.elapsed_time(t1)
+    for real, hp, hout, truth in checks:
+        if not torch.equal(hout, truth):
+            raise RuntimeError(f"e2e: {real} decode returned wrong blocks")
+        if not torch.equal(hp, wl.bufs[real][1].cpu()):
+            raise RuntimeError(f"e2e: {real} encode returned wrong parity")
+    for f in flows:
+        for ch in f["chunks"]:
+            ch["batch"].close()
     step_bytes = len(REALIZATIONS) * 2 * S * (K + M) * BLOCK
     return {"value": round(args.steps * step_bytes / (ms * 1e-3) / 1e9, 2), "unit": "GB/s",
             "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h}
