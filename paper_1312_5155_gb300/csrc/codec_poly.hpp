@@ -338,7 +338,9 @@ struct PolyDecode2 {
     for (int j = 0; j < M; ++j)
 #pragma unroll
       for (int b = 0; b < W; ++b) A[j][b] = B[j][b] = 0;
-    constexpr int U = kHornerSteps<W>;
+    // a whole renaming period per pass: no rotation fix (measured 2-4 %
+    // faster than 4-step passes with two groups)
+    constexpr int U = W;
     const int groups = (n_pos + U - 1) / U;
     const uint64_t order = bit_reverse64(read_mask) >> (64 - groups * U);
     const uint64_t live = ~((order & (~order + 1ull)) - 1ull);
