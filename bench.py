@@ -15,6 +15,10 @@ value = algorithmic bytes / time: a stripe encode moves (k+m)*B bytes
 `user_gbs` counts data bytes k*B per stripe-op.  N > 1 (torchrun): every
 rank runs the same per-GPU workload on its own stripes (weak scaling, no
 collective on the data path); value = bytes of all ranks / max rank time.
+The line also carries `e2e` (the step through the C ABI with its host
+transfers), `serve` (request latency p50 / p99 of the continuous-batching
+server at half its saturation rate) and `cpu_baseline` (the CPU oracle on
+a bounded sample of the workload).
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 """
@@ -465,6 +469,33 @@ def run_e2e(args, wl, device):
             "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h}
 
 
+SERVE_LOAD = 0.5      # fraction of the measured saturation rate
+SERVE_SECONDS = 3.0
+
+
+def run_serve():
+    """The metric's serving part on this GPU: the continuous-batching server
+    (paper_1312_5155_gb300.serve) under Poisson arrivals at SERVE_LOAD of its
+    saturation rate (measured first, every request waiting), for
+    SERVE_SECONDS; request latency p50 / p99 and the served GB/s."""
+    from paper_1312_5155_gb300 import inputs, serve
+
+    budget = 32 << 30
+    pool = serve.HostPool(2 << 30)
+    sat = serve.saturation_rate(budget, pool)
+    rate = SERVE_LOAD * sat
+    reqs = serve.make_requests(inputs.config_seed(5), rate, SERVE_SECONDS)
+    payloads = serve.make_payloads(reqs, pool)
+    results = serve.make_results(reqs, pool)
+    srv = serve.Server(budget)
+    srv.run(reqs, payloads, results)
+    summary = serve.summarize(reqs)
+    del srv
+    return {"load": SERVE_LOAD, "rate_req_per_s": round(rate, 1), "saturation_req_per_s": round(sat, 1),
+            "seconds": SERVE_SECONDS, "requests": len(reqs),
+            **{k: round(v, 4) if isinstance(v, float) else v for k, v in summary.items()}}
+
+
 # ------------------------------------------------------------ oracle arm
 def oracle_sample(seconds_target: float = 12.0):
     """Time the CPU oracle (as it stands) on whole stripes of the same
@@ -572,6 +603,7 @@ def main():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-serve", action="store_true", help="skip the serving-latency measurement")
     ap.add_argument("--no-tune", action="store_true", help="skip the launch-shape autotuner")
     ap.add_argument("--profile-case", default=None,
                     help="run one small kernel case for ncu, e.g. poly_encode, cauchy_decode")
@@ -603,6 +635,8 @@ def main():
             torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MIN)
             e2e["value"] = round(float(t.item()) * world, 2)
         result["e2e"] = e2e
+    if rank == 0 and not args.no_serve:
+        result["serve"] = run_serve()
     if rank == 0:
         if world == 1 and not args.no_cpu_baseline:
             result["cpu_baseline"] = oracle_sample()
