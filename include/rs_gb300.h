@@ -195,7 +195,9 @@ rs_status rs_batch_set_launch(rs_batch *batch, int consumer_warps, int depth, in
  * upload the descriptor tables asynchronously on `stream`.  Host-side
  * errors name the failing op and leave the previous contents in place.
  * Launch on the same stream (or synchronise) so the upload is ordered
- * before the kernels.  A CUDA graph that captured rs_batch_launch stays
+ * before the kernels.  The device tables are overwritten in place: a
+ * launch of the previous contents must be on the same stream or complete
+ * before this call's upload runs.  A CUDA graph that captured rs_batch_launch stays
  * valid after a later rs_batch_set as long as the new ops form the same
  * kernel groups in the same order (rs_batch_kernel_count and the op mix
  * unchanged): launch shapes are fixed and counts are read from device
