@@ -15,6 +15,7 @@
 #include "launch.hpp"
 #include "plan.hpp"
 #include "registry.hpp"
+#include "tile_geom.hpp"
 #include "rs_gb300.h"
 
 using namespace rsgb;
@@ -300,21 +301,6 @@ rs_status prepare_decode(rs_code* c, const int* er, int e, void* const* blocks, 
 
 // Consumer warps for a launch: the tuned value capped by the kernel.
 int pick_warps(const TuneCfg& t, int cap) { return std::max(1, std::min(t.consumer_warps, cap)); }
-
-// Bytes of the whole super-packets one packet tile can touch: a tile of T
-// units starts at a multiple of gcd(T, U) inside a super-packet of U units.
-uint32_t packet_whole_bytes(uint32_t slice, int w, int groups, uint32_t packet_bytes) {
-  const uint32_t ub = 4u * (uint32_t)groups;
-  const uint32_t T = slice / ((uint32_t)w * ub), U = packet_bytes / ub;
-  uint32_t a = T, b = U;
-  while (b) {
-    const uint32_t r = a % b;
-    a = b;
-    b = r;
-  }
-  const uint64_t touched = (uint64_t)(U - a + T - 1u) / U + 1u;
-  return (uint32_t)std::min<uint64_t>(touched * (uint64_t)w * packet_bytes, 0xFFFFFFFFull);
-}
 
 // A launch's geometry.  slice = one block's bytes of a tile; slot = the
 // ring's slot stride.  Packet tiles copy the whole super-packets they touch

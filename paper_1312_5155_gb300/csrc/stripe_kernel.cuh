@@ -40,6 +40,7 @@
 #include "job.hpp"
 #include "launch.hpp"
 #include "pipeline.cuh"
+#include "tile_geom.hpp"
 
 namespace rsgb {
 
@@ -68,45 +69,6 @@ __device__ __forceinline__ uint32_t find_stripe(const StripeDesc* st, uint32_t n
     else hi = mid;
   }
   return lo;
-}
-
-// Where tile `lt` of a stripe lies: symbol layout -> one byte range
-// [goff, goff + len) of every block; packet layout -> units
-// [lt*T, lt*T + len) (T = slice / (W*4G) units per tile), starting at column
-// col0 of the super-packet at byte goff: `head` units finish that
-// super-packet (0 when the tile starts on a boundary), `whole` complete
-// super-packets follow, then len - head - whole*U units of the next.
-struct TileGeom {
-  uint64_t goff;
-  uint32_t len;
-  uint32_t col0;
-  uint32_t head;
-  uint32_t whole;
-};
-
-template <int G>
-__device__ __forceinline__ TileGeom tile_geom(const StripeDesc& d, uint32_t lt, uint32_t slice, int w) {
-  TileGeom g;
-  g.col0 = g.head = g.whole = 0;
-  if (d.layout == kLayoutSymbol) {
-    g.goff = (uint64_t)lt * slice;
-    const uint64_t rem = d.bytes - g.goff;
-    g.len = rem < slice ? (uint32_t)rem : slice;
-  } else {
-    const uint32_t ub = 4u * (uint32_t)G;
-    const uint32_t T = slice / ((uint32_t)w * ub);
-    const uint32_t U = d.packet_bytes / ub;
-    const uint64_t total = d.bytes / ((uint64_t)w * ub);
-    const uint64_t u0 = (uint64_t)lt * T;
-    const uint64_t rem = total - u0;
-    g.len = rem < T ? (uint32_t)rem : T;
-    const uint64_t sp = u0 / U;
-    g.goff = sp * (uint64_t)w * d.packet_bytes;
-    g.col0 = (uint32_t)(u0 - sp * U);
-    g.head = g.col0 ? min(U - g.col0, g.len) : 0u;
-    g.whole = (g.len - g.head) / U;
-  }
-  return g;
 }
 
 // The per-tile operation fields a body needs, held in registers.
@@ -283,33 +245,11 @@ struct PacketTile {
     P = h.packet_bytes;
 #pragma unroll
     for (int t = 0; t < MO; ++t) outp[t] = h.outp[t];
-    const uint32_t U = P / kUnitBytes, n = h.len, head = h.head, whole = h.whole;
-    const uint32_t sp_bytes = (uint32_t)W * P;
-    valid = unit < n;
-    if (!valid) {  // reads row 0 of the slot, stores nothing
-      sbase = 0;
-      srow = 0;
-      gbase = 0;
-    } else if (whole_sp) {  // slot = the super-packets from the one at goff on
-      const uint32_t g = h.col0 + unit, j = g / U, col = g - j * U;
-      sbase = j * sp_bytes + col * kUnitBytes;
-      srow = P;
-      gbase = h.goff + (uint64_t)j * sp_bytes + (uint64_t)col * kUnitBytes;
-    } else if (unit < head) {  // leading partial super-packet
-      sbase = unit * kUnitBytes;
-      srow = head * kUnitBytes;
-      gbase = h.goff + (uint64_t)(h.col0 + unit) * kUnitBytes;
-    } else if (unit < head + whole * U) {  // whole super-packets: same layout as the block
-      const uint32_t v = unit - head, j = v / U, col = v - j * U;
-      sbase = (uint32_t)W * kUnitBytes * head + j * sp_bytes + col * kUnitBytes;
-      srow = P;
-      gbase = h.goff + (uint64_t)((head ? 1u : 0u) + j) * sp_bytes + (uint64_t)col * kUnitBytes;
-    } else {  // trailing partial super-packet
-      const uint32_t before = head + whole * U, v = unit - before;
-      sbase = (uint32_t)W * kUnitBytes * before + v * kUnitBytes;
-      srow = (n - before) * kUnitBytes;
-      gbase = h.goff + (uint64_t)((head ? 1u : 0u) + whole) * sp_bytes + (uint64_t)v * kUnitBytes;
-    }
+    const UnitPlace u = packet_unit_place<W, G>(h.goff, h.len, h.col0, h.head, h.whole, P, whole_sp, unit);
+    valid = u.valid;
+    sbase = u.sbase;
+    srow = u.srow;
+    gbase = u.gbase;
   }
 
   __device__ __forceinline__ void load(int i, uint32_t* x) {
@@ -617,39 +557,11 @@ __device__ __forceinline__ void producer_loop(const JobParams& p, const StripeDe
         } else {
           mbar_arrive(&ring.full[s]);
         }
-      } else if (p.packet_whole) {
-        // every super-packet the tile touches, in one copy
-        const uint32_t sp_bytes = (uint32_t)W * d.packet_bytes;
-        const uint32_t U = d.packet_bytes / (4u * (uint32_t)G);
-        const uint32_t bytes = ((g.col0 + g.len - 1u) / U + 1u) * sp_bytes;
-        mbar_arrive_expect_tx(&ring.full[s], bytes);
-        tma_load_1d(dst, src, bytes, &ring.full[s]);
       } else {
-        // head rows, whole super-packets, tail rows (every size a multiple
-        // of 32 units, so of 128 bytes)
-        constexpr uint32_t ub = 4u * (uint32_t)G;
-        const uint32_t P = d.packet_bytes, sp_bytes = (uint32_t)W * P;
-        const uint32_t U = P / ub;
-        const uint32_t tail = g.len - g.head - g.whole * U;
-        mbar_arrive_expect_tx(&ring.full[s], g.len * ub * (uint32_t)W);
-        uint8_t* o = dst;
-        const uint8_t* b = src;
-        if (g.head) {
-          for (int c = 0; c < W; ++c)
-            tma_load_1d(o + (size_t)c * g.head * ub, b + (size_t)c * P + (size_t)g.col0 * ub, g.head * ub,
-                        &ring.full[s]);
-          o += (size_t)W * g.head * ub;
-          b += sp_bytes;
-        }
-        if (g.whole) {
-          tma_load_1d(o, b, g.whole * sp_bytes, &ring.full[s]);
-          o += (size_t)g.whole * sp_bytes;
-          b += (size_t)g.whole * sp_bytes;
-        }
-        if (tail) {
-          for (int c = 0; c < W; ++c)
-            tma_load_1d(o + (size_t)c * tail * ub, b + (size_t)c * P, tail * ub, &ring.full[s]);
-        }
+        uint64_t* full = &ring.full[s];
+        packet_copies<W, G>(
+            g, d.packet_bytes, p.packet_whole != 0, [full](uint32_t bytes) { mbar_arrive_expect_tx(full, bytes); },
+            [dst, src, full](uint32_t so, uint32_t go, uint32_t n) { tma_load_1d(dst + so, src + go, n, full); });
       }
       ring.advance();
       ++q;

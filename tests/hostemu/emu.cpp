@@ -14,6 +14,7 @@
 #include "codec_poly.hpp"
 #include "job.hpp"
 #include "plan.hpp"
+#include "tile_geom.hpp"
 
 using namespace rsgb;
 
@@ -355,7 +356,80 @@ int mat_fixed_dispatch(int w, int k, int m, bool decode, const DecodePlan* pl, u
 
 }  // namespace
 
+// The packet-layout tile geometry of the kernel (tile_geom.hpp) over a
+// whole block: the producer's copies must stay inside the slot and the
+// block and be 16-byte aligned, every valid unit's rows in the slot must
+// hold the block bytes the unit stores to, and every unit of the block
+// must be stored exactly once.  Returns the number of violations.
+template <int W, int G>
+long check_packet_tiles(uint32_t P, int nc, int nsp, bool whole_sp) {
+  const uint32_t ub = 4u * G;
+  const uint32_t slice = (uint32_t)nc * G * segment_bytes(W);
+  const uint32_t wb = packet_whole_bytes(slice, W, G, P);
+  const uint32_t slot = whole_sp ? (wb > slice ? wb : slice) : slice;
+  const uint64_t B = (uint64_t)nsp * W * P;
+  StripeDesc d{};
+  d.layout = kLayoutPacket;
+  d.bytes = B;
+  d.packet_bytes = P;
+  const uint32_t tiles = (uint32_t)((B + slice - 1) / slice);
+  const uint32_t T = slice / (W * ub);
+  std::vector<uint8_t> covered(B / ub, 0);
+  long bad = 0;
+  for (uint32_t lt = 0; lt < tiles; ++lt) {
+    const TileGeom g = tile_geom<G>(d, lt, slice, W);
+    std::vector<int64_t> src(slot / ub, -1);
+    uint32_t total = 0;
+    int armed = 0;
+    packet_copies<W, G>(
+        g, P, whole_sp,
+        [&](uint32_t bytes) {
+          total = bytes;
+          ++armed;
+        },
+        [&](uint32_t so, uint32_t go, uint32_t n) {
+          const uint64_t at = g.goff + go;
+          if (armed != 1 || so % 16 || at % 16 || n % 16 || n == 0 || (uint64_t)so + n > slot || at + n > B) {
+            ++bad;
+            return;
+          }
+          for (uint32_t k = 0; k < n; k += ub) src[(so + k) / ub] = (int64_t)(at + k);
+        });
+    if (armed != 1) ++bad;
+    uint64_t copied = 0;
+    for (int64_t v : src) copied += v >= 0 ? ub : 0;
+    if (copied != total) ++bad;
+    for (uint32_t unit = 0; unit < T; ++unit) {
+      const UnitPlace u = packet_unit_place<W, G>(g.goff, g.len, g.col0, g.head, g.whole, P, whole_sp, unit);
+      if (u.valid != (unit < g.len)) ++bad;
+      if (!u.valid) continue;
+      for (int c = 0; c < W; ++c) {
+        const uint64_t so = u.sbase + (uint64_t)c * u.srow, at = u.gbase + (uint64_t)c * P;
+        if (so + ub > slot || at + ub > B || src[so / ub] != (int64_t)at || covered[at / ub]) {
+          ++bad;
+          continue;
+        }
+        covered[at / ub] = 1;
+      }
+    }
+  }
+  for (uint8_t c : covered) bad += c ? 0 : 1;
+  return bad;
+}
+
 extern "C" {
+
+// Packet tile geometry over one block of nsp super-packets (see
+// check_packet_tiles); -1 for arguments the library rejects.
+long emu_packet_tiles(int w, int groups, uint32_t P, int nc, int nsp, int whole_sp) {
+  if (P == 0 || P % (128u * (uint32_t)groups) || nc < 1 || nc > 16 || nsp < 1) return -1;
+  const bool ws = whole_sp != 0;
+  if (w == 8 && groups == 1) return check_packet_tiles<8, 1>(P, nc, nsp, ws);
+  if (w == 8 && groups == 2) return check_packet_tiles<8, 2>(P, nc, nsp, ws);
+  if (w == 16 && groups == 1) return check_packet_tiles<16, 1>(P, nc, nsp, ws);
+  return -1;
+}
+
 
 // Matrix realizations: kind 1 = Vandermonde (symbol layout), 2 = Cauchy
 // (packet layout, packet bytes pkt), 3 = polynomial code as a matrix
