@@ -53,13 +53,13 @@ WORKLOAD = ("RS(10,4) GF(2^8), 1 GiB data in 102 stripes of 10 x 1 MiB blocks; p
 # <op>` (16 stripes, one launch) divided by 16; a bench launch streams 102
 # stripes, so its traffic is 102 x this.  Valid only for the kernel sources
 # with the recorded digest (kernel_digest()); otherwise reported as null.
-TRAFFIC = {"digest": "82f33820e3a450ff", "per_stripe": {
-    "poly_encode": 12743808,
-    "poly_decode": 12664400,
-    "vandermonde_encode": 12702688,
-    "vandermonde_decode": 12665264,
-    "cauchy_encode": 12637088,
-    "cauchy_decode": 13303792}}
+TRAFFIC = {"digest": "6f2ce3ea6e45365f", "per_stripe": {
+    "poly_encode": 12743088,
+    "poly_decode": 12663488,
+    "vandermonde_encode": 12698432,
+    "vandermonde_decode": 12604864,
+    "cauchy_encode": 12635360,
+    "cauchy_decode": 13390512}}
 
 
 def kernel_digest() -> str:
