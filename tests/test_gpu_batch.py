@@ -129,3 +129,24 @@ def test_batch_rejects_bad_ops(rs):
     assert "op 0" in str(ei.value)
     with pytest.raises(rs.RSError):
         b.set([(code, "encode", [], list(t), 4096)] * 5)  # more than max_ops
+
+
+def test_batch_mixes_one_and_two_group_kernels(rs):
+    """Blocks on both sides of the one-/two-group threshold in one batch: the
+    same codes run as separate kernel groups and every op matches the
+    oracle."""
+    import torch
+    specs = []
+    for i, B in enumerate([64 << 10, 512 << 10, 64 << 10, 512 << 10]):
+        for real, pkt in (("vandermonde", None), ("poly", None), ("cauchy", 2048)):
+            if real == "cauchy":
+                B = (B // (8 * 2048)) * 8 * 2048
+            specs.append((real, 8, 10, 4, B, pkt, "encode" if i < 2 else "decode", 1 + i % 4))
+    codes, items = make_workload(rs, specs, seed=0x5EED0007)
+    b = rs.Batch(len(items))
+    b.set([(it["code"], it["op"], it["er"], it["rows"], it["B"]) for it in items])
+    b.launch()
+    torch.cuda.synchronize()
+    assert b.poll_status() == 0
+    check(items)
+    assert b.kernel_count >= 4
