@@ -36,11 +36,14 @@ import time
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
+from paper_1312_5155_gb300.inputs import workload_seed  # noqa: E402
+
+SEED = workload_seed("block_sizes")  # the data and erasures of this RS(10,4) 1 GiB workload
+
 K, M, W = 10, 4, 8
 BLOCK = 1 << 20
 PACKET = 2048
 DATA_BYTES = 1 << 30
-CONFIG = 2
 REALIZATIONS = ("poly", "vandermonde", "cauchy")
 METRIC = "encode/decode GB/s (poly vs Cauchy) RS(10,4) on 1 GB300, % HBM peak; serve p50/p99"
 WORKLOAD = ("RS(10,4) GF(2^8), 1 GiB data in 102 stripes of 10 x 1 MiB blocks; per realization "
@@ -190,7 +193,7 @@ class Workload:
 
         self.S = n_stripes()
         self.n = K + M
-        seed = inputs.config_seed(CONFIG)
+        seed = SEED
         self.bufs, self.batches, self.codes, self.ers, self.ops, self.shapes = {}, {}, {}, [], {}, {}
         data = torch.empty((self.S, K, BLOCK), dtype=torch.uint8, device=device)
         for s in range(self.S):
@@ -301,7 +304,7 @@ def run_ours(args, rank, world, device):
         "scaling": "weak",
         "vs_baseline": None,
         "dtype": "u8",
-        "data": "synthetic (SplitMix64 uniform-random bytes, seed 0x5EED0002)",
+        "data": f"synthetic (SplitMix64 uniform-random bytes, seed {SEED:#x})",
         "config": {"workload": WORKLOAD, "k": K, "m": M, "w": W, "block_bytes": BLOCK, "packet_bytes": PACKET,
                    "stripes_per_gpu": S, "realizations": list(REALIZATIONS),
                    "l2": "inputs (3 x 1.4 GiB) larger than L2; no flush"},
@@ -484,7 +487,7 @@ def run_serve():
     pool = serve.HostPool(2 << 30)
     sat = serve.saturation_rate(budget, pool)
     rate = SERVE_LOAD * sat
-    reqs = serve.make_requests(inputs.config_seed(5), rate, SERVE_SECONDS)
+    reqs = serve.make_requests(inputs.workload_seed("serving"), rate, SERVE_SECONDS)
     payloads = serve.make_payloads(reqs, pool)
     results = serve.make_results(reqs, pool)
     srv = serve.Server(budget)
@@ -510,7 +513,7 @@ def oracle_sample(seconds_target: float = 12.0):
 
     O.lib()
     n = K + M
-    seed = inputs.config_seed(CONFIG)
+    seed = SEED
     cores = os.cpu_count() or 1
 
     def one(s):
@@ -550,7 +553,7 @@ def run_reference(args, rank, world):
     return {
         "impl": "reference", "metric": METRIC, "value": round(v, 4), "unit": "GB/s", "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "higher_is_better": True, "scaling": "weak",
-        "vs_baseline": None, "dtype": "u8", "data": "synthetic (SplitMix64, seed 0x5EED0002)",
+        "vs_baseline": None, "dtype": "u8", "data": f"synthetic (SplitMix64, seed {SEED:#x})",
         "config": {"workload": WORKLOAD, "k": K, "m": M, "w": W, "block_bytes": BLOCK, "packet_bytes": PACKET},
         "cpu_baseline": {"value": round(v, 4), "unit": "GB/s", "cores": base["cores"], "kind": "oracle",
                          "sample": base["sample"]},
@@ -568,7 +571,7 @@ def profile_case(name: str, stripes: int = 16, launches: int = 3):
     from paper_1312_5155_gb300 import autotune, inputs, rs
 
     real, op = name.rsplit("_", 1)
-    seed = inputs.config_seed(CONFIG)
+    seed = SEED
     n = K + M
     # the launch shape the bench's autotuner chose for this op (if cached)
     sms = torch.cuda.get_device_properties(0).multi_processor_count

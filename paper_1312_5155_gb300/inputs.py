@@ -14,8 +14,8 @@ what the full-size sampled parity checks rely on.
 Byte streams are the little-endian bytes of consecutive words: byte o of a
 stream is byte (o % 8) of word (o // 8).
 
-The paper measures on random in-memory data (§5.1); the configs below mirror
-its RS(10,4) GF(2^8) setting and the block sizes of §5.2.
+The paper measures on random in-memory data (§5.1); the named workloads below
+mirror its RS(10,4) GF(2^8) setting and the block sizes of §5.2.
 """
 from __future__ import annotations
 
@@ -26,15 +26,27 @@ MIX1 = 0xBF58476D1CE4E5B9
 MIX2 = 0x94D049BB133111EB
 MASK64 = (1 << 64) - 1
 
-# Stream tags: distinct sub-streams derived from one config seed.
+# Stream tags: distinct sub-streams derived from one workload seed.
 TAG_DATA = 0x0
 TAG_ERASURE = 0xA5A5A5A5A5A5A5A5
 TAG_SHAPE = 0x5A5A5A5A5A5A5A5A
 
 
-def config_seed(config_number: int) -> int:
-    """Seed of config ``config_number`` (1-based): 0x5EED0000 + number."""
-    return 0x5EED0000 + int(config_number)
+# The synthetic workloads and the index of their seed: one RS(10,4) stripe
+# of 64 KiB blocks; RS(6,3) / RS(10,4) over 1 GiB at block sizes 4 KiB -
+# 64 MiB; RS(12,4) over GF(2^16) with 4 MiB blocks; 4096 stripes of mixed
+# codes and sizes in one batch; Poisson requests to the serving loop.
+WORKLOADS = {"single_stripe": 1, "block_sizes": 2, "gf16_blocks": 3, "mixed_batch": 4, "serving": 5}
+
+
+def stream_seed(index: int) -> int:
+    """Seed of stream ``index``: 0x5EED0000 + index."""
+    return 0x5EED0000 + int(index)
+
+
+def workload_seed(name: str) -> int:
+    """Seed of a named workload (see WORKLOADS)."""
+    return stream_seed(WORKLOADS[name])
 
 
 def _mix_np(z: np.ndarray) -> np.ndarray:
@@ -75,7 +87,7 @@ def stripe_blocks(seed: int, stripe: int, k: int, block_bytes: int,
                   col0: int = 0, ncols: int | None = None) -> np.ndarray:
     """Data blocks of one stripe as a (k, ncols) uint8 array.
 
-    The data of a config is one long byte stream cut into stripes of k blocks
+    The data of a workload is one long byte stream cut into stripes of k blocks
     of ``block_bytes``: block j of stripe s starts at byte (s*k + j)*block_bytes.
     ``col0``/``ncols`` select a column window of every block (for sampling).
     """

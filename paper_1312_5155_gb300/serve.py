@@ -381,7 +381,7 @@ def main():
     srv = Server(budget, streams=a.streams)
     for frac in [float(x) for x in a.rates.split(",")]:
         rate = frac * sat
-        reqs = make_requests(inputs.config_seed(5), rate, a.seconds)
+        reqs = make_requests(inputs.workload_seed("serving"), rate, a.seconds)
         payloads = make_payloads(reqs, pool)
         results = make_results(reqs, pool)
         srv.run(reqs, payloads, results)
@@ -390,7 +390,7 @@ def main():
             import torch
             from . import rs
             codes = {c: rs.Code(c[0], c[1], 8, "poly") for c in CODES}
-            reqs2 = make_requests(inputs.config_seed(5), rate, a.seconds)
+            reqs2 = make_requests(inputs.workload_seed("serving"), rate, a.seconds)
             serial_run(reqs2, payloads, results, codes, torch.device("cuda"), max_wall=2.0 * a.seconds)
             row["serial"] = summarize(reqs2)
         out["runs"].append(row)

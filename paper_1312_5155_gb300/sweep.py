@@ -1,4 +1,4 @@
-"""Throughput sweeps over the workload configurations of the polynomial
+"""Throughput sweeps over the synthetic workloads of the polynomial
 realization study (§5: random in-memory data, encode and decode of RS(k, m)
 stripes; §5 Fig. 1-4: block size, k and m sweeps), run through the C ABI on
 one GPU.
@@ -6,16 +6,16 @@ one GPU.
     python -m paper_1312_5155_gb300.sweep <name> [...]
 
 Names:
-  config1   RS(10,4) poly, one stripe of 10 x 64 KiB: latency of one
+  single_stripe  RS(10,4) poly, one stripe of 10 x 64 KiB: latency of one
             rs_encode / rs_decode call, and throughput of 1024 replicated
             stripes in one batched launch
-  config2   RS(6,3) and RS(10,4), GF(2^8), 1 GiB of data cut into stripes of
+  block_sizes  RS(6,3) and RS(10,4), GF(2^8), 1 GiB of data cut into stripes of
             B = 4 KiB * 2^i (i = 0..14), poly / Vandermonde / Cauchy
             (P = min(2 KiB, B/8)): batched encode, then batched decode with m
             seeded erasures per stripe
-  config3   RS(12,4) GF(2^16) little-endian, 42 stripes of 4 MiB blocks:
+  gf16_blocks  RS(12,4) GF(2^16) little-endian, 42 stripes of 4 MiB blocks:
             poly and Cauchy encode, decode with e = 1..4
-  config4   4096 stripes, (k, m) uniform over (6,3) (10,4) (12,4) (20,4),
+  mixed_batch  4096 stripes, (k, m) uniform over (6,3) (10,4) (12,4) (20,4),
             B log-uniform on [4 KiB, 8 MiB] (multiples of 4 KiB), 30 %
             decodes with e uniform in 1..m, poly: one batched launch set vs a
             loop of per-stripe rs_encode / rs_decode calls
@@ -70,7 +70,7 @@ def _time(fn, reps=10, warm=3):
 
 
 def _fill(buf, seed, k, B, stripes):
-    """Data blocks of stripes 0..stripes-1 of a config's byte stream."""
+    """Data blocks of stripes 0..stripes-1 of a workload's byte stream."""
     torch = _torch()
     per = max(1, (256 << 20) // max(1, k * B))
     for s0 in range(0, stripes, per):
@@ -122,10 +122,10 @@ def _batch_pair(real, w, k, m, B, stripes, seed, e, tune=True, tag=""):
     return out
 
 
-def config1():
+def single_stripe():
     torch = _torch()
     k, m, w, B = 10, 4, 8, 64 << 10
-    seed = inputs.config_seed(1)
+    seed = inputs.workload_seed("single_stripe")
     n = k + m
     buf = torch.empty((n, B), dtype=torch.uint8, device="cuda")
     _fill(buf.view(1, n, B), seed, k, B, 1)
@@ -134,29 +134,29 @@ def config1():
     er = inputs.erasure_pattern(seed, 0, n, m)
     lat_e = _time(lambda: code.encode(rows[:k], rows[k:], B), reps=50)
     lat_d = _time(lambda: code.decode(er, rows, B), reps=50)
-    print(json.dumps({"config": 1, "what": "one stripe, one call", "encode_us": round(lat_e * 1e3, 1),
+    print(json.dumps({"workload": "single_stripe", "what": "one stripe, one call", "encode_us": round(lat_e * 1e3, 1),
                       "decode_us": round(lat_d * 1e3, 1)}), flush=True)
     del buf
     r = _batch_pair("poly", w, k, m, B, 1024, seed, m, tag="c1-")
-    print(json.dumps({"config": 1, "what": "1024 replicated stripes, batched", **r}), flush=True)
+    print(json.dumps({"workload": "single_stripe", "what": "1024 replicated stripes, batched", **r}), flush=True)
 
 
-def config2(blocks=None, codes=((6, 3), (10, 4)), reals=("poly", "vandermonde", "cauchy")):
-    seed = inputs.config_seed(2)
+def block_sizes(blocks=None, codes=((6, 3), (10, 4)), reals=("poly", "vandermonde", "cauchy")):
+    seed = inputs.workload_seed("block_sizes")
     for (k, m) in codes:
         for i in (blocks if blocks is not None else range(15)):
             B = 4096 << i
             stripes = max(1, GIB // (k * B))
             for real in reals:
                 r = _batch_pair(real, 8, k, m, B, stripes, seed, m, tag="c2-")
-                print(json.dumps({"config": 2, "k": k, "m": m, "B": B, "stripes": stripes, "realization": real,
+                print(json.dumps({"workload": "block_sizes", "k": k, "m": m, "B": B, "stripes": stripes, "realization": real,
                                   "packet_bytes": _packet(real, 8, B), **r}), flush=True)
 
 
-def config3():
+def gf16_blocks():
     torch = _torch()
     k, m, w, B, stripes = 12, 4, 16, 4 << 20, 42
-    seed = inputs.config_seed(3)
+    seed = inputs.workload_seed("gf16_blocks")
     n = k + m
     for real in ("poly", "cauchy"):
         buf = torch.empty((stripes, n, B), dtype=torch.uint8, device="cuda")
@@ -177,14 +177,14 @@ def config3():
             res[f"decode_e{e}"] = {"ms": round(ms, 4), "gbs": round(stripes * (k + e) * B / ms / 1e6, 1)}
             d.close()
         b.close()
-        print(json.dumps({"config": 3, "realization": real, "w": w, "B": B, "stripes": stripes, **res}), flush=True)
+        print(json.dumps({"workload": "gf16_blocks", "realization": real, "w": w, "B": B, "stripes": stripes, **res}), flush=True)
         del buf
         torch.cuda.empty_cache()
 
 
-def config4(stripes=4096, reps=5):
+def mixed_batch(stripes=4096, reps=5):
     torch = _torch()
-    seed = inputs.config_seed(4)
+    seed = inputs.workload_seed("mixed_batch")
     codes = [(6, 3), (10, 4), (12, 4), (20, 4)]
     u = inputs.uniform01(inputs.shape_draws(seed, 0, 4 * stripes)).reshape(stripes, 4)
     shapes = []
@@ -219,7 +219,7 @@ def config4(stripes=4096, reps=5):
     nbytes = sum((k + m) * B if not e else (k + e) * B for k, m, B, e in shapes)
     b = rs.Batch(stripes)
     sms = torch.cuda.get_device_properties(0).multi_processor_count
-    autotune.tune_batch(b, ops, key=autotune.make_key(f"config4-{stripes}", "poly-mixed", 0, 0, 8, 1 << 20, sms))
+    autotune.tune_batch(b, ops, key=autotune.make_key(f"mixed_batch-{stripes}", "poly-mixed", 0, 0, 8, 1 << 20, sms))
     ms_batch = _time(b.launch, reps=reps, warm=2)
     if b.poll_status() != 0:
         raise RuntimeError("device status set")
@@ -237,7 +237,7 @@ def config4(stripes=4096, reps=5):
             f(*a)
 
     ms_loop = _time(loop, reps=reps, warm=1)
-    print(json.dumps({"config": 4, "stripes": stripes, "bytes": nbytes, "gib_resident": round(total / GIB, 2),
+    print(json.dumps({"workload": "mixed_batch", "stripes": stripes, "bytes": nbytes, "gib_resident": round(total / GIB, 2),
                       "decodes": sum(1 for x in shapes if x[3]), "kernel_launches_batched": b.kernel_count,
                       "batched": {"ms": round(ms_batch, 3), "gbs": round(nbytes / ms_batch / 1e6, 1)},
                       "per_stripe_loop": {"ms": round(ms_loop, 3), "gbs": round(nbytes / ms_loop / 1e6, 1)}}),
@@ -247,7 +247,7 @@ def config4(stripes=4096, reps=5):
 
 
 def kmsweep():
-    seed = inputs.config_seed(2)
+    seed = inputs.workload_seed("block_sizes")
     B = 1 << 20
     for (k, m) in [(k, 4) for k in range(2, 21)] + [(10, m) for m in (2, 3, 5, 6)]:
         stripes = max(1, GIB // (k * B))
@@ -262,7 +262,7 @@ def polyforms():
     questions: its generator matrix in the symbol layout and that matrix's
     bit-matrix projection over packets), RS(10,4) and RS(12,4) over 1 GiB
     of 1 MiB blocks."""
-    seed = inputs.config_seed(2)
+    seed = inputs.workload_seed("block_sizes")
     B = 1 << 20
     for (k, m) in ((10, 4), (12, 4), (6, 3)):
         stripes = max(1, GIB // (k * B))
@@ -274,12 +274,13 @@ def polyforms():
 
 def main():
     ap = argparse.ArgumentParser(description=__doc__, formatter_class=argparse.RawDescriptionHelpFormatter)
-    ap.add_argument("name", nargs="+", choices=["config1", "config2", "config3", "config4", "kmsweep", "polyforms"])
-    ap.add_argument("--blocks", default=None, help="config2: comma-separated exponents i (B = 4 KiB * 2^i)")
+    ap.add_argument("name", nargs="+", choices=["single_stripe", "block_sizes", "gf16_blocks", "mixed_batch", "kmsweep",
+                                                     "polyforms"])
+    ap.add_argument("--blocks", default=None, help="block_sizes: comma-separated exponents i (B = 4 KiB * 2^i)")
     a = ap.parse_args()
     for name in a.name:
-        if name == "config2" and a.blocks:
-            config2(blocks=[int(x) for x in a.blocks.split(",")])
+        if name == "block_sizes" and a.blocks:
+            block_sizes(blocks=[int(x) for x in a.blocks.split(",")])
         else:
             globals()[name]()
 

@@ -9,7 +9,7 @@ from paper_1312_5155_gb300 import inputs
 def test_staging_layout_reads_the_first_k_survivors():
     K, M = bench.K, bench.M
     S = 40
-    ers = [inputs.erasure_pattern(inputs.config_seed(2), s, K + M, M) for s in range(S)]
+    ers = [inputs.erasure_pattern(inputs.stream_seed(2), s, K + M, M) for s in range(S)]
     lay = bench.staging_layout(ers, S)
     assert len(lay) == S
     for s, (read, er) in enumerate(lay):

@@ -36,7 +36,7 @@ def test_bench_workload_sampled_parity():
     from paper_1312_5155_gb300 import build
     build.build()
     K, M, W, B, P = bench.K, bench.M, bench.W, bench.BLOCK, bench.PACKET
-    seed = inputs.config_seed(bench.CONFIG)
+    seed = bench.SEED
     wl = bench.Workload(0, torch.device("cuda:0"), tune=True)
     rng = np.random.default_rng(0x5A11)
     whole = {0, wl.S // 2, wl.S - 1}

@@ -20,7 +20,7 @@ def test_bounded_wait_reports_timeout_and_context_survives():
     build.build()
     k, m, w, B = 10, 4, 8, 1 << 20
     host = np.zeros((k + m, B), dtype=np.uint8)
-    host[:k] = inputs.stripe_blocks(inputs.config_seed(1), 9, k, B)
+    host[:k] = inputs.stripe_blocks(inputs.stream_seed(1), 9, k, B)
     ref = host.copy()
     O.poly_encode(w, k, m, ref)
     code = rs.Code(k, m, w, "poly")

@@ -24,7 +24,7 @@ def rs():
 
 def stripe(w, k, m, B, seed=7, s=0):
     host = np.zeros((k + m, B), dtype=np.uint8)
-    host[:k] = inputs.stripe_blocks(inputs.config_seed(seed), s, k, B)
+    host[:k] = inputs.stripe_blocks(inputs.stream_seed(seed), s, k, B)
     return host
 
 
@@ -73,7 +73,7 @@ def test_decode_bit_exact(rs, real, w, k, m, B, pkt, read_mode):
     n = k + m
     for s in range(m + 1):
         e = 1 + s % m
-        er = inputs.erasure_pattern(inputs.config_seed(2), s, n, e)
+        er = inputs.erasure_pattern(inputs.stream_seed(2), s, n, e)
         bad = host.copy()
         bad[er] = 0xC3
         buf, rows = device_blocks(bad)
@@ -130,7 +130,7 @@ def test_packet_tiles_any_warp_count(rs, real, w, k, m, pkt, nsp, warps):
     assert np.array_equal(to_host(buf, B), ref)
     n = k + m
     for s in range(3):
-        er = inputs.erasure_pattern(inputs.config_seed(3), s, n, m - s % 2)
+        er = inputs.erasure_pattern(inputs.stream_seed(3), s, n, m - s % 2)
         bad = ref.copy()
         bad[er] = 0xC3
         buf, rows = device_blocks(bad)

@@ -32,7 +32,7 @@ def encode_case(rs, w, k, m, B, seed=1, stripe=0, launch=None):
     if launch:
         code.set_launch(*launch)
     host = np.zeros((k + m, B), dtype=np.uint8)
-    host[:k] = inputs.stripe_blocks(inputs.config_seed(seed), stripe, k, B)
+    host[:k] = inputs.stripe_blocks(inputs.stream_seed(seed), stripe, k, B)
     ref = host.copy()
     O.poly_encode(w, k, m, ref)
     buf, rows = device_blocks(host)
@@ -84,7 +84,7 @@ def decode_case(rs, w, k, m, B, er, read_mode, seed=2, stripe=0):
     code = rs.Code(k, m, w, "poly", read_mode=read_mode)
     n = k + m
     host = np.zeros((n, B), dtype=np.uint8)
-    host[:k] = inputs.stripe_blocks(inputs.config_seed(seed), stripe, k, B)
+    host[:k] = inputs.stripe_blocks(inputs.stream_seed(seed), stripe, k, B)
     O.poly_encode(w, k, m, host)
     ref = host.copy()
     ref[er] = 0
@@ -104,7 +104,7 @@ def decode_case(rs, w, k, m, B, er, read_mode, seed=2, stripe=0):
                                      (8, 6, 3, 300001), (8, 12, 4, 1 << 19)])
 def test_decode_seeded_patterns(rs, w, k, m, B, read_mode):
     n = k + m
-    seed = inputs.config_seed(2)
+    seed = inputs.stream_seed(2)
     for stripe in range(2 * m):
         e = 1 + stripe % m
         er = inputs.erasure_pattern(seed, stripe, n, e)
@@ -129,12 +129,12 @@ def test_decode_all_patterns_rs_6_3(rs):
             assert np.array_equal(to_host(buf, B), host), er
 
 
-def test_config1_full_rs_10_4_64k(rs):
-    """Config 1: RS(10,4), GF(2^8), one stripe of 10 x 64 KiB; encode, then
-    erase 4 seeded blocks of 14 and decode."""
+def test_single_stripe_rs_10_4_64k(rs):
+    """The single-stripe workload: RS(10,4), GF(2^8), one stripe of 10 x
+    64 KiB; encode, then erase 4 seeded blocks of 14 and decode."""
     import torch
     w, k, m, B = 8, 10, 4, 65536
-    seed = inputs.config_seed(1)
+    seed = inputs.workload_seed("single_stripe")
     got, ref = encode_case(rs, w, k, m, B, seed=1)
     assert np.array_equal(got, ref)
     er = inputs.erasure_pattern(seed, 0, k + m, 4)

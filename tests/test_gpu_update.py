@@ -33,11 +33,11 @@ def test_update_equals_encode_of_new_data(rs, real, w, k, m, B, pkt):
     import torch
     code = rs.Code(k, m, w, real, packet_bytes=pkt)
     host = np.zeros((k + m, B), dtype=np.uint8)
-    host[:k] = inputs.stripe_blocks(inputs.config_seed(4), 3, k, B)
+    host[:k] = inputs.stripe_blocks(inputs.stream_seed(4), 3, k, B)
     O.encode(real, w, k, m, host, packet_bytes=pkt or 2048)
     buf, rows = device_blocks(host)
     for step, index in enumerate([0, k - 1, k // 2]):
-        new = inputs.stripe_blocks(inputs.config_seed(4), 100 + step, 1, B)[0]
+        new = inputs.stripe_blocks(inputs.stream_seed(4), 100 + step, 1, B)[0]
         delta = np.bitwise_xor(host[index], new)
         host[index] = new
         O.encode(real, w, k, m, host, packet_bytes=pkt or 2048)  # expected parity of the new data

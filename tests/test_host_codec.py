@@ -71,7 +71,7 @@ ENC_CASES = [(8, 10, 4, 65536), (8, 10, 4, 1000), (8, 6, 3, 4096 + 16), (8, 20, 
 @pytest.mark.parametrize("w,k,m,B", ENC_CASES)
 def test_encode_matches_oracle(emu, w, k, m, B):
     blocks = np.zeros((k + m, B), dtype=np.uint8)
-    blocks[:k] = inputs.stripe_blocks(inputs.config_seed(1), 0, k, B)
+    blocks[:k] = inputs.stripe_blocks(inputs.stream_seed(1), 0, k, B)
     ref = blocks.copy()
     O.poly_encode(w, k, m, ref)
     got = blocks.copy()
@@ -99,7 +99,7 @@ def test_decode_every_pattern_small_codes(emu, w, k, m, read_all):
 @pytest.mark.parametrize("w,k,m", [(8, 10, 4), (16, 12, 4), (8, 20, 4), (8, 10, 6)])
 def test_decode_seeded_patterns_match_oracle(emu, w, k, m, read_all):
     n, B = k + m, 4096 + 32
-    seed = inputs.config_seed(2)
+    seed = inputs.stream_seed(2)
     for stripe in range(6):
         blocks = np.zeros((n, B), dtype=np.uint8)
         blocks[:k] = inputs.stripe_blocks(seed, stripe, k, B)

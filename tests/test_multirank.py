@@ -25,7 +25,7 @@ def _worker(rank, world, port, out):
     from paper_1312_5155_gb300 import inputs
     S = 3
     stripes = [bench.global_stripe(rank, s, S) for s in range(S)]
-    first = inputs.stripe_blocks(inputs.config_seed(2), stripes[0], 2, 16)[0].tolist()
+    first = inputs.stripe_blocks(inputs.stream_seed(2), stripes[0], 2, 16)[0].tolist()
     t = bench.max_over_ranks(10.0 + rank, world, torch.device("cpu"))
     out[rank] = (stripes, first, t)
     dist.barrier()

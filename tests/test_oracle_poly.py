@@ -90,7 +90,7 @@ def test_every_codeword_has_the_roots(w, k, m):
     sb = 2 if w == 16 else 1
     B = 24 * sb
     blocks = np.zeros((k + m, B), dtype=np.uint8)
-    blocks[:k] = inputs.stripe_blocks(inputs.config_seed(1), 3, k, B)
+    blocks[:k] = inputs.stripe_blocks(inputs.stream_seed(1), 3, k, B)
     O.poly_encode(w, k, m, blocks)
     syms = np.stack([gfref.symbols(blocks[b], w) for b in range(k + m)])
     for t in range(syms.shape[1]):
@@ -159,7 +159,7 @@ def test_encode_equals_decode_of_erased_parity(w, k, m):
 def test_decode_round_trip_seeded_patterns(w, k, m):
     n = k + m
     B = 40
-    seed = inputs.config_seed(1)
+    seed = inputs.stream_seed(1)
     for stripe in range(12):
         blocks = np.zeros((n, B), dtype=np.uint8)
         blocks[:k] = inputs.stripe_blocks(seed, stripe, k, B)
