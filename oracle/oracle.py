@@ -67,6 +67,12 @@ def lib():
                                       ctypes.c_size_t],
                 "rso_cauchy_decode": [ctypes.c_int, ctypes.c_int, ctypes.c_int, IP, ctypes.c_int, U8P,
                                       ctypes.c_size_t, ctypes.c_size_t],
+                "rso_bitmatrix_ones": [ctypes.c_int, ctypes.c_uint32],
+                "rso_goodcauchy_matrix": [ctypes.c_int, ctypes.c_int, ctypes.c_int, U32P],
+                "rso_goodcauchy_encode": [ctypes.c_int, ctypes.c_int, ctypes.c_int, U8P, ctypes.c_size_t,
+                                          ctypes.c_size_t],
+                "rso_goodcauchy_decode": [ctypes.c_int, ctypes.c_int, ctypes.c_int, IP, ctypes.c_int, U8P,
+                                          ctypes.c_size_t, ctypes.c_size_t],
                 "rso_polymat_matrix": [ctypes.c_int, ctypes.c_int, ctypes.c_int, U32P],
                 "rso_polybm_encode": [ctypes.c_int, ctypes.c_int, ctypes.c_int, U8P, ctypes.c_size_t,
                                       ctypes.c_size_t],
@@ -222,6 +228,35 @@ def cauchy_decode(w: int, k: int, m: int, erasures, blocks: np.ndarray, packet_b
     return b
 
 
+# ------------------------------------------------- "good" Cauchy (§2.3)
+def bitmatrix_ones(w: int, e: int) -> int:
+    n = lib().rso_bitmatrix_ones(w, e)
+    if n < 0:
+        raise ValueError("bitmatrix_ones rejected its arguments")
+    return n
+
+
+def goodcauchy_matrix(w: int, k: int, m: int) -> np.ndarray:
+    C = np.zeros(m * k, dtype=np.uint32)
+    _check(lib().rso_goodcauchy_matrix(w, k, m, _p32(C)), "goodcauchy_matrix")
+    return C.reshape(m, k)
+
+
+def goodcauchy_encode(w: int, k: int, m: int, blocks: np.ndarray, packet_bytes: int) -> np.ndarray:
+    b = _blocks(blocks, k + m)
+    _check(lib().rso_goodcauchy_encode(w, k, m, b.ctypes.data_as(U8P), b.shape[1], packet_bytes),
+           "goodcauchy_encode")
+    return b
+
+
+def goodcauchy_decode(w: int, k: int, m: int, erasures, blocks: np.ndarray, packet_bytes: int) -> np.ndarray:
+    b = _blocks(blocks, k + m)
+    er = np.ascontiguousarray(np.asarray(erasures, dtype=np.int32))
+    _check(lib().rso_goodcauchy_decode(w, k, m, er.ctypes.data_as(IP), er.size, b.ctypes.data_as(U8P),
+                                       b.shape[1], packet_bytes), "goodcauchy_decode")
+    return b
+
+
 # ------------------------------------- polynomial code as a generator matrix
 def polymat_matrix(w: int, k: int, m: int) -> np.ndarray:
     Pm = np.zeros(m * k, dtype=np.uint32)
@@ -253,6 +288,8 @@ def encode(realization: str, w: int, k: int, m: int, blocks: np.ndarray, packet_
         return vand_encode(w, k, m, blocks)
     if realization == "cauchy":
         return cauchy_encode(w, k, m, blocks, packet_bytes)
+    if realization == "good_cauchy":
+        return goodcauchy_encode(w, k, m, blocks, packet_bytes)
     raise ValueError(realization)
 
 
@@ -266,4 +303,6 @@ def decode(realization: str, w: int, k: int, m: int, erasures, blocks: np.ndarra
         return vand_decode(w, k, m, erasures, blocks)
     if realization == "cauchy":
         return cauchy_decode(w, k, m, erasures, blocks, packet_bytes)
+    if realization == "good_cauchy":
+        return goodcauchy_decode(w, k, m, erasures, blocks, packet_bytes)
     raise ValueError(realization)

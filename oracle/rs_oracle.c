@@ -582,6 +582,83 @@ int rso_cauchy_decode(int w, int k, int m, const int *er, int e, uint8_t *blocks
     return rc;
 }
 
+/* ------------------------------------------- "good" Cauchy matrix (§2.3) */
+/* §2.3 notes that Cauchy matrices differ in efficiency -- the XOR count of a
+ * bit-matrix code is the number of ones of its projection -- and points to
+ * work on choosing good ones without giving a construction.  Reading taken
+ * here (the scaling heuristic of Plank and Xu's optimised Cauchy RS codes,
+ * restated): scaling a row or a column of the parity matrix by a nonzero
+ * element keeps every square submatrix nonsingular, so the code stays MDS;
+ * start from the original X = {0..m-1}, Y = {m..m+k-1} matrix, (1) divide
+ * every column by its row-0 entry (row 0 becomes all ones, the cheapest
+ * element: w ones), (2) for every other row, among the divisors 1 and the
+ * row's own entries take the one that leaves the fewest ones in the row
+ * (the first such divisor on ties) and divide the row by it. */
+static int ones_of(const field_t *f, int w, uint32_t e) {
+    int n = 0;
+    for (int c = 0; c < w; c++) {
+        uint32_t col = gmul(f, e, gpow_alpha(f, (uint64_t)c));
+        for (int r = 0; r < w; r++) n += (int)((col >> r) & 1u);
+    }
+    return n;
+}
+
+int rso_bitmatrix_ones(int w, uint32_t e) {
+    field_t *f = field_for(w);
+    if (!f) return -1;
+    return ones_of(f, w, e);
+}
+
+int rso_goodcauchy_matrix(int w, int k, int m, uint32_t *C) {
+    field_t *f;
+    if (rso_cauchy_matrix(w, k, m, C)) return -1;
+    f = field_for(w);
+    for (int j = 0; j < k; j++) {
+        uint32_t d = ginv(f, C[j]);
+        for (int i = 0; i < m; i++) C[i * k + j] = gmul(f, C[i * k + j], d);
+    }
+    for (int i = 1; i < m; i++) {
+        uint32_t best = 1;
+        long best_ones = -1;
+        for (int t = -1; t < k; t++) {
+            uint32_t v = t < 0 ? 1u : C[i * k + t];
+            uint32_t vi = ginv(f, v);
+            long ones = 0;
+            for (int j = 0; j < k; j++) ones += ones_of(f, w, gmul(f, C[i * k + j], vi));
+            if (best_ones < 0 || ones < best_ones) {
+                best_ones = ones;
+                best = v;
+            }
+        }
+        uint32_t bi = ginv(f, best);
+        for (int j = 0; j < k; j++) C[i * k + j] = gmul(f, C[i * k + j], bi);
+    }
+    return 0;
+}
+
+int rso_goodcauchy_encode(int w, int k, int m, uint8_t *blocks, size_t B, size_t P) {
+    field_t *f;
+    if (cauchy_check(w, k, m, B, P, &f)) return -1;
+    uint32_t *C = (uint32_t *)malloc(sizeof(uint32_t) * (size_t)m * k);
+    if (!C) return -3;
+    rso_goodcauchy_matrix(w, k, m, C);
+    int rc = bitmatrix_code_encode(f, w, k, m, C, blocks, B, P);
+    free(C);
+    return rc;
+}
+
+int rso_goodcauchy_decode(int w, int k, int m, const int *er, int e, uint8_t *blocks, size_t B, size_t P) {
+    field_t *f;
+    if (cauchy_check(w, k, m, B, P, &f)) return -1;
+    if (check_erasures(k + m, m, er, e)) return -1;
+    uint32_t *C = (uint32_t *)malloc(sizeof(uint32_t) * (size_t)m * k);
+    if (!C) return -3;
+    rso_goodcauchy_matrix(w, k, m, C);
+    int rc = bitmatrix_code_decode(f, w, k, m, C, er, e, blocks, B, P);
+    free(C);
+    return rc;
+}
+
 /* ------------------------------------ polynomial code as a generator matrix */
 /* §6 (third direction): a generator polynomial can be turned into a
  * generator matrix.  Column i of the m x k parity matrix holds the
