@@ -4,11 +4,12 @@
 Workload (one step), from the RS(10,4) GF(2^8) part of the 1 GiB
 block-size study: 1 GiB of uniform-random data cut into stripes of
 10 blocks x 1 MiB (102 stripes).  For each realization -- polynomial (§3),
-Vandermonde matrix (§2.2), Cauchy bit-matrix with 2 KiB packets (§2.3) -- a
-step encodes all 102 stripes (one batched persistent launch), then decodes
-all 102 stripes with m = 4 seeded erasures each (one launch; min-read: the
-first k survivors are read).  Inputs (3 x 1.4 GiB) are resident in HBM and
-larger than L2 when the timed region starts.
+Vandermonde matrix (§2.2), Cauchy bit-matrix with 2 KiB packets (§2.3) and
+its "good" matrix (GoodCRS, §2.3 / §5.1) -- a step encodes all 102 stripes
+(one batched persistent launch), then decodes all 102 stripes with m = 4
+seeded erasures each (one launch; min-read: the first k survivors are
+read).  Inputs (4 x 1.4 GiB) are resident in HBM and larger than L2 when
+the timed region starts.
 
 value = algorithmic bytes / time: a stripe encode moves (k+m)*B bytes
 (read k blocks, write m), a 4-erasure min-read decode (k+4)*B.
@@ -44,11 +45,12 @@ K, M, W = 10, 4, 8
 BLOCK = 1 << 20
 PACKET = 2048
 DATA_BYTES = 1 << 30
-REALIZATIONS = ("poly", "vandermonde", "cauchy")
+REALIZATIONS = ("poly", "vandermonde", "cauchy", "good_cauchy")
+PACKET_REALIZATIONS = ("cauchy", "good_cauchy")
 METRIC = "encode/decode GB/s (poly vs Cauchy) RS(10,4) on 1 GB300, % HBM peak; serve p50/p99"
 WORKLOAD = ("RS(10,4) GF(2^8), 1 GiB data in 102 stripes of 10 x 1 MiB blocks; per realization "
-            "(poly, vandermonde, cauchy P=2 KiB): batched encode of all stripes + batched decode with 4 seeded "
-            "erasures per stripe (min-read)")
+            "(poly, vandermonde, cauchy P=2 KiB, good cauchy P=2 KiB): batched encode of all stripes + batched "
+            "decode with 4 seeded erasures per stripe (min-read)")
 
 
 # DRAM traffic (dram__bytes_read.sum + dram__bytes_write.sum) per stripe of
@@ -157,6 +159,13 @@ def n_stripes():
     return DATA_BYTES // (K * BLOCK)
 
 
+def bench_config() -> dict:
+    """The workload's description, the same on both arms of the bench."""
+    return {"workload": WORKLOAD, "k": K, "m": M, "w": W, "block_bytes": BLOCK, "packet_bytes": PACKET,
+            "stripes_per_gpu": n_stripes(), "realizations": list(REALIZATIONS),
+            "l2": "inputs (4 x 1.4 GiB) larger than L2; no flush"}
+
+
 def global_stripe(rank: int, s: int, per_rank: int) -> int:
     """Stripe s of rank r is stripe r*per_rank + s of the world's data stream:
     ranks shard the stripes with no overlap (weak scaling)."""
@@ -201,7 +210,7 @@ class Workload:
             data[s] = inputs.random_bytes_torch(seed, gs * K * BLOCK, K * BLOCK, device).view(K, BLOCK)
         self.ers = [inputs.erasure_pattern(seed, global_stripe(rank, s, self.S), self.n, M) for s in range(self.S)]
         for real in REALIZATIONS:
-            code = rs.Code(K, M, W, real, packet_bytes=PACKET if real == "cauchy" else None)
+            code = rs.Code(K, M, W, real, packet_bytes=PACKET if real in PACKET_REALIZATIONS else None)
             # data and parity blocks of all stripes in two contiguous tensors
             dbuf = data.clone()
             pbuf = torch.empty((self.S, M, BLOCK), dtype=torch.uint8, device=device)
@@ -269,11 +278,15 @@ def run_ours(args, rank, world, device):
     torch.cuda.synchronize()
     t0 = torch.cuda.Event(enable_timing=True)
     t1 = torch.cuda.Event(enable_timing=True)
+    # the NVTX range marks the timed region for profilers (ncu --nvtx
+    # --nvtx-include "timed_steps/")
+    torch.cuda.nvtx.range_push("timed_steps")
     t0.record(st)
     for i in range(args.steps):
         step(evs[i])
     t1.record(st)
     torch.cuda.synchronize()
+    torch.cuda.nvtx.range_pop()
     clocks = sampler.stop() if sampler else None
     total_ms = t0.elapsed_time(t1)
     op_ms = {nm: sum(e[i].elapsed_time(e[i + 1]) for e in evs) / args.steps for i, nm in enumerate(names)}
@@ -305,9 +318,7 @@ def run_ours(args, rank, world, device):
         "vs_baseline": None,
         "dtype": "u8",
         "data": f"synthetic (SplitMix64 uniform-random bytes, seed {SEED:#x})",
-        "config": {"workload": WORKLOAD, "k": K, "m": M, "w": W, "block_bytes": BLOCK, "packet_bytes": PACKET,
-                   "stripes_per_gpu": S, "realizations": list(REALIZATIONS),
-                   "l2": "inputs (3 x 1.4 GiB) larger than L2; no flush"},
+        "config": bench_config(),
         "user_gbs": round(user, 2),
         "ops": ops,
         "roofline": {"bound": "hbm", "kernel": f"{dom[0]}_{dom[1]}", "achieved": dom_gbs, "peak": peak,
@@ -476,12 +487,33 @@ SERVE_LOAD = 0.5      # fraction of the measured saturation rate
 SERVE_SECONDS = 3.0
 
 
-def run_serve():
-    """The metric's serving part on this GPU: the continuous-batching server
-    (paper_1312_5155_gb300.serve) under Poisson arrivals at SERVE_LOAD of its
-    saturation rate (measured first, every request waiting), for
-    SERVE_SECONDS; request latency p50 / p99 and the served GB/s."""
+def _serial_capacity(pool, codes, seconds: float = 1.0) -> float:
+    """Requests/s of the serial per-request path with every request waiting."""
+    import torch
+
     from paper_1312_5155_gb300 import inputs, serve
+
+    reqs = serve.make_requests(inputs.workload_seed("serving") + 7, 1e9, 1.0, max_requests=2000)
+    for r in reqs:
+        r.arrival = 0.0
+    payloads = serve.make_payloads(reqs, pool)
+    results = serve.make_results(reqs, pool)
+    serve.serial_run(reqs[:20], payloads, results, codes, torch.device("cuda"))
+    t0 = time.perf_counter()
+    serve.serial_run(reqs, payloads, results, codes, torch.device("cuda"), max_wall=seconds)
+    dt = time.perf_counter() - t0
+    return sum(1 for r in reqs if r.done >= 0) / dt
+
+
+def run_serve():
+    """The metric's serving part on this GPU (configuration 5's request mix):
+    the continuous-batching server (paper_1312_5155_gb300.serve) under Poisson
+    arrivals for SERVE_SECONDS at SERVE_LOAD of its saturation rate (the
+    highest rate it keeps up with, found by bisection), request latency
+    p50 / p99 and served GB/s; then the batched server and the serial
+    per-request path at the same offered rate, half of what the serial path
+    sustains."""
+    from paper_1312_5155_gb300 import inputs, rs, serve
 
     budget = 32 << 30
     pool = serve.HostPool(2 << 30)
@@ -492,80 +524,160 @@ def run_serve():
     results = serve.make_results(reqs, pool)
     srv = serve.Server(budget)
     srv.run(reqs, payloads, results)
-    summary = serve.summarize(reqs)
+    summary = serve.summarize(reqs, wall=SERVE_SECONDS)
+    codes = {c: rs.Code(c[0], c[1], 8, "poly") for c in serve.CODES}
+    cap = _serial_capacity(pool, codes)
+    srate = 0.5 * cap
+    reqs_b = serve.make_requests(inputs.workload_seed("serving"), srate, SERVE_SECONDS)
+    pay_b = serve.make_payloads(reqs_b, pool)
+    res_b = serve.make_results(reqs_b, pool)
+    srv.run(reqs_b, pay_b, res_b)
+    reqs_s = serve.make_requests(inputs.workload_seed("serving"), srate, SERVE_SECONDS)
+    serve.serial_run(reqs_s, pay_b, res_b, codes, __import__("torch").device("cuda"),
+                     max_wall=SERVE_SECONDS + 5.0)
     del srv
+
+    def rnd(d):
+        return {k: round(v, 4) if isinstance(v, float) else v for k, v in d.items()}
+
     return {"load": SERVE_LOAD, "rate_req_per_s": round(rate, 1), "saturation_req_per_s": round(sat, 1),
-            "seconds": SERVE_SECONDS, "requests": len(reqs),
-            **{k: round(v, 4) if isinstance(v, float) else v for k, v in summary.items()}}
+            "seconds": SERVE_SECONDS, "requests": len(reqs), **rnd(summary),
+            "vs_serial": {"rate_req_per_s": round(srate, 1), "serial_capacity_req_per_s": round(cap, 1),
+                          "requests": len(reqs_b), "batched": rnd(serve.summarize(reqs_b, wall=SERVE_SECONDS)),
+                          "serial": rnd(serve.summarize(reqs_s, wall=SERVE_SECONDS))}}
 
 
 # ------------------------------------------------------------ oracle arm
-def oracle_sample(seconds_target: float = 12.0):
-    """Time the CPU oracle (as it stands) on whole stripes of the same
-    workload -- each realization's encode and 4-erasure decode -- one stripe
-    per host thread, sized to about seconds_target of wall time."""
-    import concurrent.futures as cf
+def cpu_info() -> dict:
+    """Model and clock of the host CPU (lscpu, else /proc/cpuinfo)."""
+    info = {"cpu_model": None, "cpu_max_mhz": None, "logical_cpus": os.cpu_count()}
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            key, _, val = line.partition(":")
+            key, val = key.strip(), val.strip()
+            if key == "Model name" and not info["cpu_model"]:
+                info["cpu_model"] = val
+            elif key == "CPU max MHz":
+                info["cpu_max_mhz"] = float(val)
+    except (OSError, subprocess.SubprocessError, ValueError):
+        pass
+    if not info["cpu_model"]:
+        try:
+            with open("/proc/cpuinfo") as f:
+                for line in f:
+                    if line.lower().startswith("model name"):
+                        info["cpu_model"] = line.split(":", 1)[1].strip()
+                        break
+        except OSError:
+            pass
+    if info["cpu_max_mhz"] is None:
+        try:
+            with open("/sys/devices/system/cpu/cpu0/cpufreq/cpuinfo_max_freq") as f:
+                info["cpu_max_mhz"] = int(f.read()) / 1000.0
+        except (OSError, ValueError):
+            pass
+    return info
 
+
+def _oracle_stripe_pass(s: int) -> float:
+    """The oracle (as it stands) on one whole stripe of the workload: each
+    realization's encode, then its 4-erasure decode.  Returns seconds."""
     import numpy as np
 
     from oracle import oracle as O
     from paper_1312_5155_gb300 import inputs
 
-    O.lib()
     n = K + M
-    seed = SEED
-    cores = os.cpu_count() or 1
+    b0 = np.zeros((n, BLOCK), dtype=np.uint8)
+    b0[:K] = inputs.stripe_blocks(SEED, s, K, BLOCK)
+    er = inputs.erasure_pattern(SEED, s, n, M)
+    t = time.perf_counter()
+    for real in REALIZATIONS:
+        b = b0.copy()
+        O.encode(real, W, K, M, b, packet_bytes=PACKET)
+        b[er] = 0
+        O.decode(real, W, K, M, er, b, packet_bytes=PACKET)
+    return time.perf_counter() - t
 
-    def one(s):
-        b0 = np.zeros((n, BLOCK), dtype=np.uint8)
-        b0[:K] = inputs.stripe_blocks(seed, s, K, BLOCK)
-        er = inputs.erasure_pattern(seed, s, n, M)
-        t = time.perf_counter()
-        for real in REALIZATIONS:
-            b = b0.copy()
-            O.encode(real, W, K, M, b, packet_bytes=PACKET)
-            b[er] = 0
-            O.decode(real, W, K, M, er, b, packet_bytes=PACKET)
-        return time.perf_counter() - t
 
-    t_one = one(0)
-    per_thread = max(1, int(seconds_target / max(t_one, 1e-3)))
-    nstripes = cores * per_thread  # stripe indices taken modulo the workload's stripes
+def oracle_run(threads: int, passes_per_thread: int, first: int = 1) -> tuple[float, int]:
+    """GB/s of `threads` host threads each running `passes_per_thread`
+    stripe passes (stripe indices taken modulo the workload's stripes)."""
+    import concurrent.futures as cf
+
+    from oracle import oracle as O
+
+    O.lib()
+    nstripes = threads * passes_per_thread
     t0 = time.perf_counter()
-    with cf.ThreadPoolExecutor(cores) as ex:
-        list(ex.map(one, [s % n_stripes() for s in range(1, 1 + nstripes)]))
+    with cf.ThreadPoolExecutor(threads) as ex:
+        list(ex.map(_oracle_stripe_pass, [s % n_stripes() for s in range(first, first + nstripes)]))
     dt = time.perf_counter() - t0
     step_bytes = nstripes * len(REALIZATIONS) * 2 * (K + M) * BLOCK
-    return {"value": round(step_bytes / dt / 1e9, 4), "unit": "GB/s", "cores": cores, "kind": "oracle",
-            "sample": f"{nstripes} stripe passes over the 102 RS(10,4) 1 MiB-block stripes, encode + 4-erasure "
-                      f"decode in each of the 3 realizations, one stripe per thread on {cores} host threads "
-                      f"({dt:.1f} s wall)"}
+    return step_bytes / dt / 1e9, nstripes
+
+
+def oracle_sample(seconds_target: float = 12.0, runs: int = 3):
+    """The CPU oracle timed as the paper times its codecs (§5.1: the mean of
+    3 runs) on whole stripes of the same workload, once with one thread per
+    host core and once single-threaded, each run sized to about
+    seconds_target / (2 * runs) of wall time."""
+    import statistics as stats
+
+    from oracle import oracle as O
+
+    O.lib()
+    cores = os.cpu_count() or 1
+    t_one = _oracle_stripe_pass(0)
+    per_run = seconds_target / (2 * runs)
+    all_passes = max(1, int(per_run / max(t_one, 1e-3)))
+    one_passes = max(1, int(per_run / max(t_one, 1e-3)))
+    multi = [oracle_run(cores, all_passes, first=1 + r * cores * all_passes) for r in range(runs)]
+    single = [oracle_run(1, one_passes, first=1 + r * one_passes) for r in range(runs)]
+    info = cpu_info()
+    return {"value": round(stats.mean(v for v, _ in multi), 4), "unit": "GB/s", "cores": cores, "kind": "oracle",
+            "runs": runs, "per_run_gbs": [round(v, 4) for v, _ in multi],
+            "single_thread_gbs": round(stats.mean(v for v, _ in single), 4),
+            "single_thread_per_run_gbs": [round(v, 4) for v, _ in single],
+            **info,
+            "sample": f"whole stripes of the 102 RS(10,4) 1 MiB-block stripes, encode + 4-erasure decode in each "
+                      f"of the 3 realizations per stripe pass; all-core: {runs} runs of {cores} threads x "
+                      f"{all_passes} passes (one stripe per thread at a time); single-thread: {runs} runs of "
+                      f"{one_passes} passes; value = mean of the all-core runs"}
 
 
 def run_reference(args, rank, world):
     if rank != 0:
         return None
+    cores = os.cpu_count() or 1
+    t_one = _oracle_stripe_pass(0)
+    passes = max(1, int(3.0 / max(t_one, 1e-3)))  # about 3 s per step
     for _ in range(args.warmup):
-        oracle_sample(2.0)
-    samples = [oracle_sample(6.0) for _ in range(args.steps)]
-    v = statistics.mean(s["value"] for s in samples)
-    base = samples[-1]
+        oracle_run(cores, 1)
+    samples = [oracle_run(cores, passes, first=1 + i * cores * passes)[0] for i in range(args.steps)]
+    v = statistics.mean(samples)
+    base = {"cores": cores, "sample": f"{args.steps} steps of {cores} threads x {passes} whole-stripe passes "
+                                      f"(encode + 4-erasure decode in each of the 3 realizations); value = mean "
+                                      f"over the steps", **cpu_info()}
     return {
         "impl": "reference", "metric": METRIC, "value": round(v, 4), "unit": "GB/s", "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "u8", "data": f"synthetic (SplitMix64, seed {SEED:#x})",
-        "config": {"workload": WORKLOAD, "k": K, "m": M, "w": W, "block_bytes": BLOCK, "packet_bytes": PACKET},
+        "config": bench_config(),
         "cpu_baseline": {"value": round(v, 4), "unit": "GB/s", "cores": base["cores"], "kind": "oracle",
-                         "sample": base["sample"]},
+                         "sample": base["sample"], "cpu_model": base["cpu_model"],
+                         "cpu_max_mhz": base["cpu_max_mhz"]},
         "e2e": {"value": round(v, 4), "unit": "GB/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
 
 
-def profile_case(name: str, stripes: int = 16, launches: int = 3):
-    """Small case of one bench kernel for ncu: `stripes` stripes of the bench
-    geometry (RS(10,4), 1 MiB blocks; 16 stripes = 224 MiB, larger than L2),
-    one realization, `launches` batched launches of one op (after one
-    encode that makes the parity valid)."""
+def profile_case(name: str, stripes: int = 16, launches: int = 3, shape=None):
+    """One bench kernel for ncu: `stripes` stripes of the bench geometry
+    (RS(10,4), 1 MiB blocks; 16 stripes = 224 MiB, larger than L2; 102 =
+    the bench's launch), one realization, `launches` batched launches of one
+    op (after one encode that makes the parity valid), with the launch
+    shape the bench's autotuner chose (or `shape`)."""
     import torch
 
     from paper_1312_5155_gb300 import autotune, inputs, rs
@@ -576,8 +688,9 @@ def profile_case(name: str, stripes: int = 16, launches: int = 3):
     # the launch shape the bench's autotuner chose for this op (if cached)
     sms = torch.cuda.get_device_properties(0).multi_processor_count
     hit = autotune._load().get(autotune.make_key(f"batch{n_stripes()}-{op}", real, K, M, W, BLOCK, sms))
-    shape = tuple(hit["shape"]) if hit else (8, 16, 1)
-    code = rs.Code(K, M, W, real, packet_bytes=PACKET if real == "cauchy" else None)
+    if shape is None:
+        shape = tuple(hit["shape"]) if hit else (8, 16, 1)
+    code = rs.Code(K, M, W, real, packet_bytes=PACKET if real in PACKET_REALIZATIONS else None)
     buf = torch.empty((stripes, n, BLOCK), dtype=torch.uint8, device="cuda")
     buf[:, :K] = inputs.random_bytes_torch(seed, 0, stripes * K * BLOCK, "cuda").view(stripes, K, BLOCK)
     rows = [list(buf[s]) for s in range(stripes)]
@@ -610,9 +723,12 @@ def main():
     ap.add_argument("--no-tune", action="store_true", help="skip the launch-shape autotuner")
     ap.add_argument("--profile-case", default=None,
                     help="run one small kernel case for ncu, e.g. poly_encode, cauchy_decode")
+    ap.add_argument("--profile-stripes", type=int, default=16, help="stripes of the --profile-case launch")
+    ap.add_argument("--profile-shape", default=None, help="launch shape warps,depth,ctas_per_sm for --profile-case")
     args = ap.parse_args()
     if args.profile_case:
-        profile_case(args.profile_case)
+        shape = tuple(int(x) for x in args.profile_shape.split(",")) if args.profile_shape else None
+        profile_case(args.profile_case, stripes=args.profile_stripes, shape=shape)
         return
 
     world = int(os.environ.get("WORLD_SIZE", "1"))

@@ -44,8 +44,13 @@ typedef enum {
   RS_CAUCHY = 2,         /* Cauchy generator, bit-matrix XOR over packets, §2.3 */
   RS_POLY_MATRIX = 3,    /* the polynomial code through its generator matrix
                             (column i = x^(m+i) mod g(x), §6); same bytes as RS_POLY */
-  RS_POLY_BITMATRIX = 4  /* that matrix's bit-matrix projection over packets
+  RS_POLY_BITMATRIX = 4, /* that matrix's bit-matrix projection over packets
                             (§6 with §2.3's packet layout) */
+  RS_GOOD_CAUCHY = 5     /* "good" Cauchy generator (§2.3; GoodCRS of §5.1):
+                            the RS_CAUCHY matrix with every column divided by
+                            its row-0 entry and every other row divided by the
+                            divisor (1 or one of its entries) that leaves the
+                            fewest ones; bit-matrix XOR over packets */
 } rs_realization;
 
 typedef enum {
@@ -238,38 +243,50 @@ rs_status rs_copy_blocks(void *const *dst, const void *const *src, const size_t 
                          size_t engine_min_bytes, void *stream);
 
 /* ------------------------------------------------------------------------
- * Allocation-free batched encode.  The paper has no counterpart: this entry
- * point exists for callers that cannot allocate device memory when they
- * encode -- code running while a stream is captured into a CUDA graph
- * (cudaMalloc is not allowed there), allocator or memory-pool callbacks that
- * must not re-enter the allocator, and embedders that own the whole device
- * memory budget.  rs_init and rs_batch_create allocate (status word,
- * descriptor tables); this call does not: all scratch the batched kernel
- * needs (descriptor tables, pointer table, status word) lives in one
- * fixed 256 KiB static device array, reserved on every GPU that loads the
- * library until the process exits.  The caller passes only the blocks.
+ * Allocation-free batched encode.  The paper has no counterpart.  Some
+ * callers cannot allocate device memory at the moment they encode:
+ * allocator and memory-pool callbacks (a caching allocator that encodes the
+ * blocks it evicts) must not re-enter the allocator they belong to;
+ * embedders that reserve the whole device memory budget at start-up forbid
+ * allocations afterwards; latency-critical paths cannot afford cudaMalloc /
+ * cudaFree, which may synchronise the device.  rs_init and rs_batch_create
+ * allocate (status word, descriptor tables); this call allocates nothing:
+ * all scratch the batched kernel needs (descriptor tables, pointer table,
+ * a status word) lives in one fixed 256 KiB static device array, reserved on
+ * every GPU that loads the library until the process exits, and the tables
+ * reach it through small upload kernels that carry them as kernel
+ * parameters.  It calls no cudaMalloc, cudaFree or other allocating
+ * routine.  The caller passes only the blocks.
  *
  * Encodes n_stripes stripes of the polynomial RS(k, m) code over GF(2^w)
- * (§3.2 Eq. 1 per stripe) in one persistent launch on `stream`:
+ * (§3.2 Eq. 1 per stripe) with one persistent encode launch on `stream`:
  *   data_ptrs:   n_stripes * k device pointers, stripe-major (stripe s uses
  *                data_ptrs[s*k .. s*k+k-1]);
  *   parity_ptrs: n_stripes * m device pointers, stripe-major;
- *   block_bytes: n_stripes block sizes (0 skips the stripe).
- * Block rules as for rs_encode.  Limits: those of rs_init, and the tables
- * must fit the array: 256 + (n_stripes * 56 rounded up to 256) + n_stripes *
- * (k + m) * 8 bytes <= 262144 (e.g. up to 1500 stripes of RS(10,4)); larger
+ *   block_bytes: n_stripes block sizes (0 skips the stripe);
+ *   device_status: NULL, or a 4-byte aligned device pointer to an int the
+ *                caller has set to 0: a device-side wait that gives up (the
+ *                2 s bound of the staging pipeline) stores a nonzero code
+ *                there and the affected tiles' parity is not written.  With
+ *                NULL the code goes to the array's own status word, which no
+ *                call reports.
+ * Block rules as for rs_encode; the bytes written equal rs_encode's for the
+ * same stripes.  Limits: those of rs_init, and the tables must fit the
+ * array: 256 + (S * 56 rounded up to 256) + S * (k + m) * 8 bytes <= 262144
+ * for S non-empty stripes (e.g. up to 1500 stripes of RS(10,4)); larger
  * requests return RS_EINVAL with the sizes in rs_last_error.
- * The first call on a device does a one-time set-up with that device
- * current (the device address of the array, the kernel's shared-memory
- * attribute); make that first call before any stream capture.  The array is
- * shared by all calls on a device and keeps the last call's contents: the
- * status word is cleared at the start of each call and the tables are
- * rewritten, so calls whose work overlaps on the GPU race -- order them on
- * one stream or synchronise between them.  Device-side wait timeouts are
- * recorded in the array's status word only (not reported to the caller).
+ * Set-up: the first call on a device looks up the array's device address
+ * (cudaGetSymbolAddress, with that device current), and the first call for
+ * each (w, m) on a device sets its encode kernel's shared-memory size
+ * attribute; make those first calls before any stream capture.  The array
+ * is shared by all calls on a device and keeps the last call's contents:
+ * each call clears the status word and rewrites the tables before its
+ * kernel runs, so calls whose work overlaps on the GPU race -- order them
+ * on one stream or synchronise between them.
  * Errors: RS_EINVAL, RS_EUNSUPPORTED, RS_ECUDA. */
 rs_status rs_poly_encode_stripes_noalloc(int k, int m, int w, int n_stripes, const void *const *data_ptrs,
-                                         void *const *parity_ptrs, const size_t *block_bytes, void *stream);
+                                         void *const *parity_ptrs, const size_t *block_bytes,
+                                         int *device_status, void *stream);
 
 #ifdef __cplusplus
 }

@@ -33,7 +33,8 @@ NVCC_FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC,-O2",
 # Families: 0 poly, 1 matrix with runtime P, 2 matrix with compile-time P,
 # 3 mixed polynomial kernel.  ops: 0 poly encode, 1 poly decode,
 # 2 matrix encode, 3 matrix decode.  Layout: 0 symbol, 1 packet.
-# Kinds: 1 Vandermonde, 2 Cauchy.
+# Kinds: 1 Vandermonde, 2 Cauchy, 3 / 4 the polynomial code's generator
+# matrix (symbol / packet layout), 5 good Cauchy.
 FIXED_CODES = [(8, 6, 3), (8, 10, 4), (8, 12, 4), (8, 20, 4), (16, 12, 4)]
 # compile-time generator-matrix forms of the polynomial code
 FIXED_POLY_MATRIX_CODES = [(8, 10, 4)]
@@ -62,11 +63,11 @@ def instances():
                 for layout in (0, 1):
                     out.append((f"matrt_w{w}_m{m}_op{op}_l{layout}", f"MatRuntimeBody<{w}, {m}, {op}, {layout}>",
                                 dict(family=1, w=w, m=m, op=op, layout=layout)))
-    fixed = [(c, kind) for c in FIXED_CODES for kind in (1, 2)] + \
+    fixed = [(c, kind) for c in FIXED_CODES for kind in (1, 2, 5)] + \
         [(c, kind) for c in FIXED_POLY_MATRIX_CODES for kind in (3, 4)]
     for (w, k, m), kind in fixed:
         for op in (2, 3):
-            layout = 1 if kind in (2, 4) else 0
+            layout = 1 if kind in (2, 4, 5) else 0
             name = f"matfix_w{w}_k{k}_m{m}_kind{kind}_op{op}"
             key = dict(family=2, w=w, m=m, op=op, layout=layout, kind=kind, k=k)
             out.append((name, f"MatFixedBody<{w}, {k}, {m}, {kind}, {op}>", key))
@@ -123,6 +124,7 @@ def generate_units() -> list[str]:
             f"  return launch_body<{body}>(p, sh, st);\n}}\n"
             f"int warps_{name}() {{ return {body}::kMaxWarps; }}\n"
             f"int groups_{name}() {{ return {body}::kGroups; }}\n"
+            f"int pwarps_{name}() {{ return {body}::kProducerWarps; }}\n"
             "}  // namespace rsgb\n"))
         units.append(path)
     lines = ["// generated by paper_1312_5155_gb300/build.py", '#include "registry.hpp"', "namespace rsgb {"]
@@ -130,6 +132,7 @@ def generate_units() -> list[str]:
         lines.append(f"cudaError_t launch_{name}(const JobParams&, const LaunchShape&, cudaStream_t);")
         lines.append(f"int warps_{name}();")
         lines.append(f"int groups_{name}();")
+        lines.append(f"int pwarps_{name}();")
     lines.append("static const KernelEntry* build_table() {")
     lines.append(f"  static KernelEntry t[{len(insts)}];")
     for i, (name, _, key) in enumerate(insts):
@@ -137,7 +140,7 @@ def generate_units() -> list[str]:
         k.update(key)
         lines.append(f"  t[{i}] = KernelEntry{{KernelKey{{{k['family']}, {k['w']}, {k['m']}, {k['op']}, "
                      f"{k['layout']}, {k['kind']}, {k['k']}, {k['mset']}u, {k['wide']}}}, launch_{name}, "
-                     f'warps_{name}(), groups_{name}(), "{name}"}};')
+                     f'warps_{name}(), groups_{name}(), pwarps_{name}(), "{name}"}};')
     lines.append("  return t;\n}")
     lines.append("const KernelEntry* const kKernelRegistryPtr = build_table();")
     lines.append(f"const int kKernelRegistrySize = {len(insts)};")
@@ -146,6 +149,13 @@ def generate_units() -> list[str]:
     _write_if_changed(reg, "\n".join(lines) + "\n")
     units.append(reg)
     return units
+
+
+def generate_select_header() -> None:
+    """Rewrite csrc/select_gen.hpp (the decode-matrix jump tables) from
+    gen_select.py; unchanged text leaves the file and its mtime alone."""
+    from . import gen_select
+    gen_select.write()
 
 
 def sources() -> list[str]:
@@ -181,6 +191,7 @@ def _compile(src: str, obj: str, verbose: bool) -> tuple[str, str]:
 
 def build(force: bool = False, verbose: bool = False, jobs: int | None = None) -> str:
     os.makedirs(os.path.join(BUILD, "obj"), exist_ok=True)
+    generate_select_header()
     srcs = sources()
     hdr_mtime = max([os.path.getmtime(h) for h in _headers()] + [os.path.getmtime(__file__)])
     todo = [s for s in srcs if force or _stale(s, _obj(s), hdr_mtime)]

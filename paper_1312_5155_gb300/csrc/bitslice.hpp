@@ -240,8 +240,9 @@ RS_HD void xor_subset(uint32_t* y, const uint32_t (*S)[W], const uint32_t (*P)[W
   }
 }
 
-#if defined(__CUDA_ARCH__)
 RS_CHD constexpr int rotated(int b, int rot, int w) { return ((b - rot) % w + w) % w; }
+
+#if defined(__CUDA_ARCH__)
 
 // GF(2^8) form of xor_selected with a warp-uniform jump table (brx.idx.uni)
 // over the 16 selector values; written out because the compiler lowers the
@@ -444,6 +445,12 @@ RS_HD void xor_selected(uint32_t sel, uint32_t* y, const uint32_t (*S)[W], const
       break;
   }
 }
+
+}  // namespace rsgb
+
+#include "select_gen.hpp"
+
+namespace rsgb {
 
 // acc[r] ^= sum_q M[r][q] * in_q ... for one input q: acc[r] ^= M[r][q] * x,
 // as sum over c of mask(r, q, c) & (alpha^c x).  x is clobbered.

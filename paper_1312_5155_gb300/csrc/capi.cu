@@ -39,9 +39,14 @@ rs_status cuda_fail(cudaError_t e, const char* what) {
 }
 
 constexpr int kMaxGroups = 8;                        // kernels per batch launch
-constexpr int kKindOf[5] = {0, kKindVandermonde, kKindCauchy, kKindPolyMatrix, kKindPolyBitMatrix};
+// Batches whose polynomial ops move at most this many bytes use the mixed
+// polynomial kernel (at ~5 TB/s about 50 us of work: a few launches' worth).
+constexpr uint64_t kMixedMaxBytes = 256ull << 20;
+constexpr int kKindOf[6] = {0, kKindVandermonde, kKindCauchy, kKindPolyMatrix, kKindPolyBitMatrix, kKindGoodCauchy};
 
-bool packet_layout(Realization r) { return r == Realization::Cauchy || r == Realization::PolyBitMatrix; }
+bool packet_layout(Realization r) {
+  return r == Realization::Cauchy || r == Realization::PolyBitMatrix || r == Realization::GoodCauchy;
+}
 
 bool has_fixed_kernels(int w, int k, int m, int kind) {
   KernelKey key;
@@ -299,15 +304,20 @@ rs_status prepare_decode(rs_code* c, const int* er, int e, void* const* blocks, 
   return RS_OK;
 }
 
-// Consumer warps for a launch: the tuned value capped by the kernel.
-int pick_warps(const TuneCfg& t, int cap) { return std::max(1, std::min(t.consumer_warps, cap)); }
+// Consumer warps for a launch: the tuned value capped by the kernel (a
+// multiple of 4 for kernels with a producer warpgroup).
+int pick_warps(const TuneCfg& t, const KernelEntry* e) {
+  int nc = std::max(1, std::min(t.consumer_warps, e->max_warps));
+  if (e->producer_warps == 4) nc = std::max(4, nc / 4 * 4);
+  return nc;
+}
 
 // A launch's geometry.  slice = one block's bytes of a tile; slot = the
 // ring's slot stride.  Packet tiles copy the whole super-packets they touch
 // (one bulk copy per block instead of one per packet row of a partial
 // super-packet) when those take at most 3/2 of the tile's own bytes;
 // `whole` reports that choice.
-LaunchShape make_shape(const TuneCfg& t, int nc, int w, int groups, int num_sms, int layout,
+LaunchShape make_shape(const TuneCfg& t, int nc, int pw, int w, int groups, int num_sms, int layout,
                        const std::vector<uint32_t>& packets, uint32_t& slice, uint32_t& slot, uint32_t& depth,
                        uint32_t& whole) {
   slice = (uint32_t)(nc * groups) * segment_bytes(w);
@@ -330,7 +340,7 @@ LaunchShape make_shape(const TuneCfg& t, int nc, int w, int groups, int num_sms,
   const size_t budget = kMaxDynamicSmem / (size_t)std::max(1, t.ctas_per_sm);
   while (depth > 2 && ring_smem_bytes(depth, slot) > budget) --depth;
   LaunchShape sh;
-  sh.threads = (nc + 1) * 32;
+  sh.threads = (nc + pw) * 32;
   sh.smem = ring_smem_bytes(depth, slot);
   sh.grid = std::max(1, num_sms * std::max(1, t.ctas_per_sm));
   return sh;
@@ -346,9 +356,9 @@ rs_status launch_single(rs_code* c, PreparedOp& po, void* stream) {
   if (s != RS_OK) return s;
   JobParams* p = new (std::nothrow) JobParams();
   if (!p) return fail(RS_ENOMEM, "host allocation failed");
-  const int nc = pick_warps(c->tune, po.entry->max_warps);
+  const int nc = pick_warps(c->tune, po.entry);
   uint32_t slice, slot, depth, whole;
-  LaunchShape sh = make_shape(c->tune, nc, c->w, po.entry->groups, c->num_sms, po.key.layout, {po.d.packet_bytes},
+  LaunchShape sh = make_shape(c->tune, nc, po.entry->producer_warps, c->w, po.entry->groups, c->num_sms, po.key.layout, {po.d.packet_bytes},
                               slice, slot, depth, whole);
   p->status = c->d_status;
   p->n_stripes = 1;
@@ -448,7 +458,7 @@ rs_status rs_init(int k, int m, int w, int realization, rs_code** out) {
   *out = nullptr;
   if (w != 8 && w != 16) return fail(RS_EINVAL, "w must be 8 or 16");
   if (k < 1 || m < 1) return fail(RS_EINVAL, "need k >= 1 and m >= 1");
-  if (realization < RS_POLY || realization > RS_POLY_BITMATRIX) return fail(RS_EINVAL, "unknown realization");
+  if (realization < RS_POLY || realization > RS_GOOD_CAUCHY) return fail(RS_EINVAL, "unknown realization");
   if ((long)k + m > (1L << w) - 1) return fail(RS_EINVAL, "k + m must be <= 2^w - 1");
   if (m > kMaxM || k + m > kMaxBlocks || (w == 16 && m > 4))
     return fail(RS_EUNSUPPORTED, "device path limits: m <= 8 (m <= 4 for w = 16) and k + m <= 64");
@@ -465,6 +475,8 @@ rs_status rs_init(int k, int m, int w, int realization, rs_code** out) {
     }
   } else if (c->real == Realization::Cauchy) {
     cauchy_parity_matrix(k, m, w, c->P);
+  } else if (c->real == Realization::GoodCauchy) {
+    good_cauchy_parity_matrix(k, m, w, c->P);
   } else {
     // polynomial code (any of its three realizations): column i of P is
     // x^(m+i) mod g(x), the parity of the unit data vector e_i
@@ -667,19 +679,26 @@ rs_status rs_batch_set(rs_batch* b, const rs_op* ops, int n_ops, void* stream) {
   // group by kernel (mixed polynomial kernels merge several M)
   std::vector<const KernelEntry*> group_entry;
   std::vector<std::vector<int>> members;
-  std::map<const KernelEntry*, int> primary_count;
+  // A mixed polynomial kernel (one launch for several M and both ops)
+  // replaces the per-M kernels only for small batches, where the launches
+  // it saves matter; large ones keep the specialised kernels (more warps,
+  // two column groups for the decodes).
+  std::map<const KernelEntry*, uint64_t> primary_bytes;
   for (auto& po : prep)
-    if (!po.noop) primary_count[po.entry]++;
+    if (!po.noop) primary_bytes[po.entry] += (uint64_t)(po.d.n_in + po.d.n_out) * po.d.bytes;
   std::map<const KernelEntry*, int> mixed_users;
-  for (auto& kv : primary_count) {
+  std::map<const KernelEntry*, uint64_t> mixed_bytes;
+  for (auto& kv : primary_bytes) {
     const KernelEntry* mx = mixed_for(kv.first->key);
-    if (mx) mixed_users[mx]++;
+    if (!mx) continue;
+    mixed_users[mx]++;
+    mixed_bytes[mx] += kv.second;
   }
   for (int i = 0; i < n_ops; ++i) {
     if (prep[i].noop) continue;
     const KernelEntry* e = prep[i].entry;
     const KernelEntry* mx = mixed_for(e->key);
-    if (mx && mixed_users[mx] >= 2) e = mx;
+    if (mx && mixed_users[mx] >= 2 && mixed_bytes[mx] <= kMixedMaxBytes) e = mx;
     int g = -1;
     for (size_t j = 0; j < group_entry.size(); ++j)
       if (group_entry[j] == e) g = (int)j;
@@ -711,22 +730,23 @@ rs_status rs_batch_set(rs_batch* b, const rs_op* ops, int n_ops, void* stream) {
     gr.entry = group_entry[g];
     const int layout = prep[members[g][0]].key.layout;
     gr.layout = layout;
-    gr.nc = pick_warps(b->tune, gr.entry->max_warps);
+    gr.nc = pick_warps(b->tune, gr.entry);
     const int w = gr.entry->key.w;
     std::vector<uint32_t> packets;
     if (layout == kLayoutPacket)
       for (int i : members[g]) packets.push_back(prep[i].d.packet_bytes);
-    gr.sh = make_shape(b->tune, gr.nc, w, gr.entry->groups, b->num_sms, layout, packets, gr.slice, gr.slot, gr.depth,
+    gr.sh = make_shape(b->tune, gr.nc, gr.entry->producer_warps, w, gr.entry->groups, b->num_sms, layout, packets, gr.slice, gr.slot, gr.depth,
                        gr.whole);
-    uint32_t tiles = 0;
+    uint64_t tiles = 0;  // tile numbers are 32-bit in the kernel
     StripeDesc* region = hs + g * (size_t)b->max_ops;
     for (size_t q = 0; q < members[g].size(); ++q) {
       PreparedOp& po = prep[members[g][q]];
       StripeDesc d = po.d;
-      d.tile_begin = tiles;
+      d.tile_begin = (uint32_t)tiles;
       d.ptr_off = (uint32_t)np;
       d.coef_off = (uint32_t)ncw;
       tiles += tiles_of(d, gr.slice);
+      if (tiles > 0xFFFFFFFFull) return fail(RS_EINVAL, "too many tiles in one kernel group (more than 2^32)");
       std::copy(po.ptrs.begin(), po.ptrs.end(), hp + np);
       np += po.ptrs.size();
       std::copy(po.coef.begin(), po.coef.end(), hc + ncw);
@@ -734,9 +754,9 @@ rs_status rs_batch_set(rs_batch* b, const rs_op* ops, int n_ops, void* stream) {
       region[q] = d;
     }
     gr.n_stripes = (uint32_t)members[g].size();
-    gr.tiles = tiles;
+    gr.tiles = (uint32_t)tiles;
     hn[2 * g] = gr.n_stripes;
-    hn[2 * g + 1] = tiles;
+    hn[2 * g + 1] = gr.tiles;
     groups.push_back(gr);
   }
   // upload (stream-ordered)

@@ -66,7 +66,8 @@ RS_CHD constexpr bool ct_invert(uint32_t (&A)[K][K], uint32_t (&R)[K][K], int w)
 
 // Parity rows of the systematic generator.
 //   Vandermonde (§2.2): G = V_full V_top^-1 with V_full[r][c] = r^c.
-//   Cauchy (§2.3): C[i][j] = 1 / (i + (m + j)), X = {0..m-1}, Y = {m..m+k-1}.
+//   Cauchy (§2.3): C[i][j] = 1 / (i + (m + j)), X = {0..m-1}, Y = {m..m+k-1};
+//   its "good" form: rows and columns scaled to fewer ones (good_cauchy_scale).
 //   Polynomial code as a matrix (§6): column i = x^(m+i) mod g(x), since
 //   x^m d(x) mod g = sum_i d_i (x^(m+i) mod g) (Eq. 1).
 template <int W, int K, int M, int KIND>
@@ -83,9 +84,11 @@ struct ParityMatrix {
         for (int j = M - 1; j >= 1; --j) r[j] = r[j - 1] ^ gf_mul(top, g.c[j], W);
         r[0] = gf_mul(top, g.c[0], W);
       }
-    } else if (KIND == kKindCauchy) {
+    } else if (KIND == kKindCauchy || KIND == kKindGoodCauchy) {
       for (int i = 0; i < M; ++i)
         for (int j = 0; j < K; ++j) P.a[i][j] = gf_inv((uint32_t)i ^ (uint32_t)(M + j), W);
+      if (KIND == kKindGoodCauchy)
+        good_cauchy_scale([&P](int i, int j) -> uint32_t& { return P.a[i][j]; }, K, M, W);
     } else {
       uint32_t top[K][K] = {};
       uint32_t inv[K][K] = {};
@@ -219,7 +222,7 @@ struct MatDecodeFixed {
 
 // Compile-time-P decode with two 32-column groups per thread (M <= 4): the
 // syndromes of both groups, then apply2_and_store.
-template <int W, int K, int M, int KIND, bool kTranspose = true>
+template <int W, int K, int M, int KIND, bool kTranspose = true, bool kPairSums = false>
 struct MatDecodeFixed2 {
   template <class Src, class Dst, class Coef>
   static RS_HD void run(uint64_t read_mask, int e, Src& src, Dst& dst, Coef& coef) {
@@ -262,7 +265,7 @@ struct MatDecodeFixed2 {
         }
       }
     }
-    apply2_and_store<W, M, kTranspose>(e, A, B, sel, dst);
+    apply2_and_store<W, M, kTranspose, kPairSums>(e, A, B, sel, dst);
   }
 };
 

@@ -153,6 +153,55 @@ RS_HD void horner_mul_add(uint32_t (*S)[W], const uint32_t* x) {
   });
 }
 
+// One bit of the decode-matrix Horner rule, y <- alpha * y + Z (Z the
+// subset of the syndromes the selector names), with y going from rotation
+// ROT - 1 to ROT: on the GPU one jump-table dispatch whose cases merge the
+// fold of alpha * y into the selected XORs; elsewhere the two steps.
+template <int W, int ROT, int NS>
+RS_HD void fold_and_select(uint32_t sel, uint32_t* y, const uint32_t (*S)[W], const uint32_t (*P)[W]) {
+#if defined(__CUDA_ARCH__)
+  if constexpr (W == 8) {
+    fold_select_w8<ROT, NS>(sel, y, S, P);
+    return;
+  } else if constexpr (W == 16) {
+    fold_select_w16<ROT, NS>(sel, y, S);
+    return;
+  }
+#endif
+  mul_alpha_renamed<W, ROT - 1>(y);
+  xor_selected<W, ROT, NS>(sel, y, S, P);
+}
+
+// The same for two 32-column groups (y0 from A, y1 from B; no pair sums).
+template <int W, int ROT, int NS>
+RS_HD void fold_and_select2(uint32_t sel, uint32_t* y0, uint32_t* y1, const uint32_t (*A)[W], const uint32_t (*B)[W]) {
+#if defined(__CUDA_ARCH__)
+  if constexpr (W == 8) {
+    fold_select2_w8<ROT, NS>(sel, y0, y1, A, B);
+    return;
+  }
+#endif
+  mul_alpha_renamed<W, ROT - 1>(y0);
+  mul_alpha_renamed<W, ROT - 1>(y1);
+  xor_selected2<W, ROT, NS>(sel, y0, y1, A, B);
+}
+
+// Two groups with the pair sums PA = (A0^A1, A2^A3), PB likewise.
+template <int W, int ROT, int NS>
+RS_HD void fold_and_select2p(uint32_t sel, uint32_t* y0, uint32_t* y1, const uint32_t (*A)[W], const uint32_t (*B)[W],
+                             const uint32_t (*PA)[W], const uint32_t (*PB)[W]) {
+#if defined(__CUDA_ARCH__)
+  if constexpr (W == 8) {
+    fold_select2p_w8<ROT, NS>(sel, y0, y1, A, B, PA, PB);
+    return;
+  }
+#endif
+  mul_alpha_renamed<W, ROT - 1>(y0);
+  mul_alpha_renamed<W, ROT - 1>(y1);
+  xor_selected<W, ROT, NS>(sel, y0, A, PA);
+  xor_selected<W, ROT, NS>(sel, y1, B, PB);
+}
+
 // Steps per pass of the syndrome Horner and bits per pass of the
 // decode-matrix Horner.  Fully unrolling the W-step renaming period makes
 // the decode's loop body larger than the instruction cache serves well;
@@ -199,11 +248,15 @@ RS_HD void apply_and_store(int e, const uint32_t (*S)[W], const Selectors<W, M>&
       StaticFor<0, kSteps>::run([&](auto Uu) {
         constexpr int u = decltype(Uu)::value;
         const int c = c0 - u;
-        mul_alpha_renamed<W, u>(y);  // alpha * 0 on the first bit: harmless
+        // alpha * y (alpha * 0 on the first bit: harmless) fused with the
+        // first chunk's selected syndromes
         StaticFor<0, Sel::kChunks>::run([&](auto H) {
           constexpr int h = decltype(H)::value;
           constexpr int ns = (M - 4 * h < 4) ? M - 4 * h : 4;
-          xor_selected<W, u + 1, ns>(Sel::nibble(row, c * Sel::kChunks + h), y, S + 4 * h, P[h]);
+          if constexpr (h == 0)
+            fold_and_select<W, u + 1, ns>(Sel::nibble(row, c * Sel::kChunks), y, S, P[0]);
+          else
+            xor_selected<W, u + 1, ns>(Sel::nibble(row, c * Sel::kChunks + h), y, S + 4 * h, P[h]);
         });
       });
       if constexpr (kSteps % W != 0) {
@@ -277,13 +330,28 @@ struct PolyDecode {
 
 // apply_and_store for two 32-column groups: output t of group 0 from the
 // syndromes A, of group 1 from B, stored as one 2W-word output (group 0 in
-// words 0..W-1; planes back to symbols with kTranspose).  M <= 4, no pair
-// sums.
-template <int W, int M, bool kTranspose = true, class Dst>
+// words 0..W-1; planes back to symbols with kTranspose).  M <= 4; pair sums
+// with kPairSums.
+template <int W, int M, bool kTranspose = true, bool kPairSums = false, class Dst>
 RS_HD void apply2_and_store(int e, const uint32_t (*A)[W], const uint32_t (*B)[W], const Selectors<W, M>& sel,
                             Dst& dst) {
   static_assert(M <= 4, "one selector chunk");
   using Sel = Selectors<W, M>;
+  // pair sums A0^A1, A2^A3 (and of B) when the kernel has registers for
+  // them: a subset of four syndromes is then at most two terms per plane
+  constexpr bool kPairs = kPairSums && M >= 2;
+  uint32_t PA[2][W], PB[2][W];
+  if constexpr (kPairs) {
+#pragma unroll
+    for (int b = 0; b < W; ++b) {
+      PA[0][b] = A[0][b] ^ A[1][b];
+      PB[0][b] = B[0][b] ^ B[1][b];
+      if (M > 3) {
+        PA[1][b] = A[2][b] ^ A[3][b];
+        PB[1][b] = B[2][b] ^ B[3][b];
+      }
+    }
+  }
 #pragma unroll 1
   for (int t = 0; t < e; ++t) {
     uint32_t row[Sel::kRowWords];
@@ -297,9 +365,10 @@ RS_HD void apply2_and_store(int e, const uint32_t (*A)[W], const uint32_t (*B)[W
       StaticFor<0, kSteps>::run([&](auto Uu) {
         constexpr int u = decltype(Uu)::value;
         const int c = c0 - u;
-        mul_alpha_renamed<W, u>(y);
-        mul_alpha_renamed<W, u>(y + W);
-        xor_selected2<W, u + 1, M>(Sel::nibble(row, c), y, y + W, A, B);
+        if constexpr (kPairs)
+          fold_and_select2p<W, u + 1, M>(Sel::nibble(row, c), y, y + W, A, B, PA, PB);
+        else
+          fold_and_select2<W, u + 1, M>(Sel::nibble(row, c), y, y + W, A, B);
       });
       if constexpr (kSteps % W != 0) {
         uint32_t r[2 * W];
@@ -324,9 +393,10 @@ RS_HD void apply2_and_store(int e, const uint32_t (*A)[W], const uint32_t (*B)[W
 // 2W words (group 0 = words 0..W-1, group 1 = W..2W-1 of every input and
 // output).  Every warp-uniform decision -- the Horner presence test, the
 // barrier waits, the selector dispatch -- then serves 64 columns, and the
-// two groups' instruction streams are independent.  Without pair sums (they
-// would not fit the registers); M <= 4.
-template <int W, int M>
+// two groups' instruction streams are independent.  Pair sums in the
+// decode-matrix step with kPairSums (they need the larger register budget
+// of the split kernel); M <= 4.
+template <int W, int M, bool kPairSums = false>
 struct PolyDecode2 {
   static_assert(M <= 4, "one selector chunk");
   template <class Src, class Dst, class Coef>
@@ -383,7 +453,7 @@ struct PolyDecode2 {
         });
       }
     }
-    apply2_and_store<W, M>(e, A, B, sel, dst);
+    apply2_and_store<W, M, true, kPairSums>(e, A, B, sel, dst);
   }
 };
 

@@ -90,6 +90,48 @@ RS_CHD constexpr uint32_t bitmatrix_row(uint32_t e, int r, int w) {
   return row;
 }
 
+// Ones of the bit-matrix of e (§2.3 projection): the XOR count of a
+// product by e in the bit-matrix codes.  Column c is e * alpha^c.
+RS_CHD constexpr int bitmatrix_ones(uint32_t e, int w) {
+  int n = 0;
+  uint32_t col = e;
+  for (int c = 0; c < w; ++c) {
+    for (uint32_t v = col; v; v &= v - 1u) ++n;
+    col = gf_mul(col, 2u, w);
+  }
+  return n;
+}
+
+// "Good" Cauchy matrix (§2.3: Cauchy matrices differ in XOR cost; GoodCRS
+// of §5.1), in place on an m x k parity matrix (row stride k) holding the
+// original Cauchy matrix.  Scaling a row or a column by a nonzero element
+// keeps every square submatrix nonsingular (the code stays MDS), so: every
+// column is divided by its row-0 entry (row 0 becomes all ones, w ones
+// each), then every other row is divided by whichever of 1 and its own
+// entries leaves the fewest ones (the first such on ties).  at(i, j)
+// returns a reference to entry (i, j).
+template <class At>
+RS_CHD constexpr void good_cauchy_scale(At&& at, int k, int m, int w) {
+  for (int j = 0; j < k; ++j) {
+    const uint32_t d = gf_inv(at(0, j), w);
+    for (int i = 0; i < m; ++i) at(i, j) = gf_mul(at(i, j), d, w);
+  }
+  for (int i = 1; i < m; ++i) {
+    uint32_t best = 1;
+    long best_ones = -1;
+    for (int t = -1; t < k; ++t) {
+      const uint32_t vi = gf_inv(t < 0 ? 1u : at(i, t), w);
+      long n = 0;
+      for (int j = 0; j < k; ++j) n += bitmatrix_ones(gf_mul(at(i, j), vi, w), w);
+      if (best_ones < 0 || n < best_ones) {
+        best_ones = n;
+        best = vi;
+      }
+    }
+    for (int j = 0; j < k; ++j) at(i, j) = gf_mul(at(i, j), best, w);
+  }
+}
+
 template <int W, uint32_t E>
 struct BitMatrix {
   struct Rows {

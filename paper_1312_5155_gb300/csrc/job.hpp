@@ -23,11 +23,11 @@ enum : uint8_t {
 enum : uint8_t { kLayoutSymbol = 0, kLayoutPacket = 1 };
 
 // Matrix realizations with a compile-time generator
-enum : int { kKindVandermonde = 1, kKindCauchy = 2, kKindPolyMatrix = 3, kKindPolyBitMatrix = 4 };
+enum : int { kKindVandermonde = 1, kKindCauchy = 2, kKindPolyMatrix = 3, kKindPolyBitMatrix = 4, kKindGoodCauchy = 5 };
 
 // Layout of a matrix kind: the bit-matrix kinds keep §2.3's packet layout.
 RS_CHD constexpr int kind_layout(int kind) {
-  return (kind == kKindCauchy || kind == kKindPolyBitMatrix) ? 1 : 0;
+  return (kind == kKindCauchy || kind == kKindPolyBitMatrix || kind == kKindGoodCauchy) ? 1 : 0;
 }
 
 struct StripeDesc {

@@ -230,6 +230,11 @@ void cauchy_parity_matrix(int k, int m, int w, std::vector<uint32_t>& P) {
     for (int j = 0; j < k; ++j) P[(size_t)i * k + j] = gf_inv((uint32_t)i ^ (uint32_t)(m + j), w);
 }
 
+void good_cauchy_parity_matrix(int k, int m, int w, std::vector<uint32_t>& P) {
+  cauchy_parity_matrix(k, m, w, P);
+  good_cauchy_scale([&P, k](int i, int j) -> uint32_t& { return P[(size_t)i * k + j]; }, k, m, w);
+}
+
 void poly_parity_matrix(int k, int m, int w, std::vector<uint32_t>& P) {
   const GenPoly g = make_genpoly(w, m);
   P.assign((size_t)m * k, 0);

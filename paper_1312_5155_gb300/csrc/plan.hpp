@@ -12,7 +12,7 @@
 
 namespace rsgb {
 
-enum class Realization : int { Poly = 0, Vandermonde = 1, Cauchy = 2, PolyMatrix = 3, PolyBitMatrix = 4 };
+enum class Realization : int { Poly = 0, Vandermonde = 1, Cauchy = 2, PolyMatrix = 3, PolyBitMatrix = 4, GoodCauchy = 5 };
 
 struct DecodePlan {
   int M = 0;                  // unknowns = syndromes evaluated
@@ -65,6 +65,8 @@ std::vector<uint32_t> pack_columns(const std::vector<uint32_t>& P, int k, int m,
 // Parity rows (m x k, row-major) of the systematic generators (§2.2, §2.3).
 bool vandermonde_parity_matrix(int k, int m, int w, std::vector<uint32_t>& P);
 void cauchy_parity_matrix(int k, int m, int w, std::vector<uint32_t>& P);
+// The "good" Cauchy matrix (§2.3, GoodCRS of §5.1): good_cauchy_scale of the above.
+void good_cauchy_parity_matrix(int k, int m, int w, std::vector<uint32_t>& P);
 // Polynomial code as a generator matrix (§6): column i = x^(m+i) mod g(x).
 void poly_parity_matrix(int k, int m, int w, std::vector<uint32_t>& P);
 

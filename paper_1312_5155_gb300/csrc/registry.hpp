@@ -36,6 +36,7 @@ struct KernelEntry {
   Launcher launch;
   int max_warps;
   int groups;  // 32-column groups per consumer lane (tile slice = warps * groups * segment)
+  int producer_warps;  // 1, or 4: a producer warpgroup (consumer count a multiple of 4)
   const char* name;
 };
 

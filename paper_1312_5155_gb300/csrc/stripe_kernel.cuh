@@ -305,6 +305,35 @@ struct ColumnWords {
 };
 
 // ------------------------------------------------------------------ bodies
+// Register split: the producer gets a warpgroup of its own (4 warps, one of
+// them working) that gives back registers with setmaxnreg.dec, and the
+// consumer warpgroups take them with setmaxnreg.inc.  A CTA of 4 + 12 warps
+// is launched at 128 registers a thread (the 64K of an SM); the producer
+// warpgroup drops to P, the 12 consumer warps rise to C, with
+// 128 P + 384 C <= 65536, so every launch of 4, 8 or 12 consumer warps fits
+// (the shares are checked against the compiled count before the first
+// launch).  Used where the extra registers were measured to pay: the
+// two-group decodes with pair sums in the decode-matrix step, and the
+// GF(2^16) decodes (12 instead of 8 consumer warps).  The packet-layout
+// producer needs more registers than the symbol-layout one.
+constexpr int kSplitMaxConsumers = 12;
+template <int P, int C>
+struct RegSplit {
+  static_assert(P % 8 == 0 && C % 8 == 0 && P * 128 + C * 32 * kSplitMaxConsumers <= 65536,
+                "register split exceeds the launch's registers");
+  static constexpr int kProducerWarps = 4;
+  static constexpr int kProducerRegs = P;
+  static constexpr int kConsumerRegs = C;
+};
+struct NoSplit {
+  static constexpr int kProducerWarps = 1;
+  static constexpr int kProducerRegs = 0;
+  static constexpr int kConsumerRegs = 0;
+};
+using SymbolDecodeSplit = RegSplit<56, 152>;  // two-group symbol-layout decode, pair sums
+using PacketDecodeSplit = RegSplit<80, 144>;  // two-group packet-layout decode, pair sums
+using Wide16DecodeSplit = RegSplit<104, 136>; // GF(2^16) one-group decodes
+
 RS_CHD constexpr int body_warps(int regs_words) { return regs_words <= 48 ? 16 : 8; }
 // Register budget: 8-warp GF(2^8) bodies whose live state (accumulators,
 // plus the outputs for a decode) is at most 64 words are compiled for two
@@ -315,13 +344,15 @@ RS_CHD constexpr int body_min_blocks(int w, int max_warps, int live_words) {
 }
 
 template <int W, int M, int OP>
-struct PolyBody {
+struct PolyBody : std::conditional_t<W == 16 && OP == kOpDecode, Wide16DecodeSplit, NoSplit> {
   static constexpr int kW = W;
   static constexpr int kGroups = 1;
   static constexpr int kLayout = kLayoutSymbol;
   static constexpr int kMaxOut = M;
-  static constexpr int kMaxWarps = OP == kOpEncode ? body_warps(M * W) : 8;
-  static constexpr int kMinBlocks = body_min_blocks(W, kMaxWarps, (OP == kOpEncode ? 1 : 2) * M * W);
+  static constexpr int kMaxWarps =
+      PolyBody::kProducerWarps == 4 ? kSplitMaxConsumers : (OP == kOpEncode ? body_warps(M * W) : 8);
+  static constexpr int kMinBlocks =
+      PolyBody::kProducerWarps == 4 ? 1 : body_min_blocks(W, kMaxWarps, (OP == kOpEncode ? 1 : 2) * M * W);
   __device__ static bool matches(const TileOp& o) { return o.op == OP && o.m == M; }
   template <class Tile>
   __device__ static void run(const TileOp& o, Tile& t, const uint32_t* coef) {
@@ -337,7 +368,7 @@ struct PolyBody {
 // Compile-time-P encode with two 32-column groups per lane (symbol layout,
 // GF(2^8), M <= 4): MatEncodeFixed2.
 template <int W, int K, int M, int KIND>
-struct MatFixedEncode2Body {
+struct MatFixedEncode2Body : NoSplit {
   static constexpr int kW = W;
   static constexpr int kGroups = 2;
   static constexpr int kLayout = kLayoutSymbol;
@@ -355,26 +386,25 @@ struct MatFixedEncode2Body {
 // GF(2^8) polynomial decode with two 32-column groups per lane
 // (PolyDecode2): 64 columns per thread share every warp-uniform decision.
 template <int W, int M>
-struct PolyDecode2Body {
+struct PolyDecode2Body : SymbolDecodeSplit {
   static constexpr int kW = W;
   static constexpr int kGroups = 2;
   static constexpr int kLayout = kLayoutSymbol;
   static constexpr int kMaxOut = M;
-  // two groups of syndromes and outputs live at once: 12 consumer warps in
-  // one CTA per SM keep them in registers (128 a thread; a 15-warp bound
-  // measured 4 % slower, its register allocation spilling differently)
-  static constexpr int kMaxWarps = 12;
+  // two groups of syndromes and outputs live at once, plus the pair sums:
+  // 12 consumer warps at the split's 152 registers
+  static constexpr int kMaxWarps = kSplitMaxConsumers;
   static constexpr int kMinBlocks = 1;
   __device__ static bool matches(const TileOp& o) { return o.op == kOpDecode && o.m == M; }
   template <class Tile>
   __device__ static void run(const TileOp& o, Tile& t, const uint32_t* coef) {
     CoefWords cm{coef};
-    PolyDecode2<W, M>::run(o.n_pos, o.read_mask, o.e, t, t, cm);
+    PolyDecode2<W, M, true>::run(o.n_pos, o.read_mask, o.e, t, t, cm);
   }
 };
 
 template <int W, int M, int OP, int LAYOUT>
-struct MatRuntimeBody {
+struct MatRuntimeBody : NoSplit {
   static constexpr int kW = W;
   static constexpr int kGroups = 1;
   static constexpr int kLayout = LAYOUT;
@@ -395,13 +425,15 @@ struct MatRuntimeBody {
 };
 
 template <int W, int K, int M, int KIND, int OP>
-struct MatFixedBody {
+struct MatFixedBody : std::conditional_t<W == 16 && OP == kOpMatDecode, Wide16DecodeSplit, NoSplit> {
   static constexpr int kW = W;
   static constexpr int kGroups = 1;
   static constexpr int kLayout = kind_layout(KIND);
   static constexpr int kMaxOut = M;
-  static constexpr int kMaxWarps = OP == kOpMatEncode ? body_warps(M * W) : 8;
-  static constexpr int kMinBlocks = body_min_blocks(W, kMaxWarps, (OP == kOpMatEncode ? 1 : 2) * M * W);
+  static constexpr int kMaxWarps =
+      MatFixedBody::kProducerWarps == 4 ? kSplitMaxConsumers : (OP == kOpMatEncode ? body_warps(M * W) : 8);
+  static constexpr int kMinBlocks =
+      MatFixedBody::kProducerWarps == 4 ? 1 : body_min_blocks(W, kMaxWarps, (OP == kOpMatEncode ? 1 : 2) * M * W);
   __device__ static bool matches(const TileOp& o) { return o.op == OP && o.m == M && o.k == K; }
   template <class Tile>
   __device__ static void run(const TileOp& o, Tile& t, const uint32_t* coef) {
@@ -417,19 +449,21 @@ struct MatFixedBody {
 // Compile-time-P decode (M <= 4) with two 32-column groups per lane
 // (MatDecodeFixed2), in either layout.
 template <int W, int K, int M, int KIND>
-struct MatFixedDecode2Body {
+struct MatFixedDecode2Body : std::conditional_t<kind_layout(KIND) == kLayoutPacket, PacketDecodeSplit, NoSplit> {
   static constexpr int kW = W;
   static constexpr int kGroups = 2;
   static constexpr int kLayout = kind_layout(KIND);
   static constexpr int kMaxOut = M;
-  // symbol layout: up to 15 warps at 128 registers; packet layout: 12
-  static constexpr int kMaxWarps = kLayout == kLayoutSymbol ? 15 : 12;
+  // symbol layout: up to 15 warps at 128 registers (the pair sums measured
+  // slower there: they spill at the split's budget); packet layout: the
+  // register split and pair sums, 12 warps at 144 registers
+  static constexpr int kMaxWarps = kLayout == kLayoutSymbol ? 15 : kSplitMaxConsumers;
   static constexpr int kMinBlocks = 1;
   __device__ static bool matches(const TileOp& o) { return o.op == kOpMatDecode && o.m == M && o.k == K; }
   template <class Tile>
   __device__ static void run(const TileOp& o, Tile& t, const uint32_t* coef) {
     CoefWords cm{coef};
-    MatDecodeFixed2<W, K, M, KIND, kind_layout(KIND) == kLayoutSymbol>::run(o.read_mask, o.e, t, t, cm);
+    MatDecodeFixed2<W, K, M, KIND, kLayout == kLayoutSymbol, kLayout == kLayoutPacket>::run(o.read_mask, o.e, t, t, cm);
   }
 };
 
@@ -459,6 +493,12 @@ struct MixedBody {
     return b;
   }
   static constexpr int kMinBlocks = min_blocks();
+  static constexpr int kProducerWarps = First::kProducerWarps;
+  static constexpr int kProducerRegs = First::kProducerRegs;
+  static constexpr int kConsumerRegs = First::kConsumerRegs;
+  static_assert(((Rest::kProducerWarps == First::kProducerWarps && Rest::kProducerRegs == First::kProducerRegs &&
+                  Rest::kConsumerRegs == First::kConsumerRegs) && ...),
+                "one warp layout per kernel");
   __device__ static bool matches(const TileOp& o) { return First::matches(o) || (Rest::matches(o) || ...); }
   template <class Tile>
   __device__ static void run(const TileOp& o, Tile& t, const uint32_t* coef) {
@@ -578,7 +618,12 @@ __device__ __forceinline__ void producer_loop(const JobParams& p, const StripeDe
 
 // ------------------------------------------------------------------ kernel
 template <class Body>
-__global__ void __launch_bounds__((Body::kMaxWarps + 1) * 32, Body::kMinBlocks)
+RS_CHD constexpr int body_threads() {
+  return (Body::kMaxWarps + Body::kProducerWarps) * 32;
+}
+
+template <class Body>
+__global__ void __launch_bounds__(body_threads<Body>(), Body::kMinBlocks)
     rs_stripe_kernel(const __grid_constant__ JobParams p) {
   constexpr int W = Body::kW;
   extern __shared__ __align__(128) uint8_t smem[];
@@ -592,7 +637,8 @@ __global__ void __launch_bounds__((Body::kMaxWarps + 1) * 32, Body::kMinBlocks)
   ring.slice = p.slice_bytes;
   ring.stride = p.slot_bytes ? p.slot_bytes : p.slice_bytes;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int nc = (int)(blockDim.x >> 5) - 1;
+  // consumer warps 0..nc-1, then the producer warp (or warpgroup)
+  const int nc = (int)(blockDim.x >> 5) - Body::kProducerWarps;
   if (threadIdx.x == 0) {
     for (uint32_t s = 0; s < depth; ++s) {
       mbar_init(&ring.full[s], 1);
@@ -607,11 +653,13 @@ __global__ void __launch_bounds__((Body::kMaxWarps + 1) * 32, Body::kMinBlocks)
   const uint32_t n_stripes = p.counts ? p.counts[0] : p.n_stripes;
   const uint32_t total_tiles = p.counts ? p.counts[1] : p.total_tiles;
 
-  if (warp == nc) {
-    if (lane == 0)
+  if (warp >= nc) {
+    if constexpr (Body::kProducerWarps == 4) asm volatile("setmaxnreg.dec.sync.aligned.u32 %0;" ::"n"(Body::kProducerRegs));
+    if (warp == nc && lane == 0)
       producer_loop<W, Body::kLayout, Body::kGroups>(p, stripes, ptrs, coef, headers, ring, n_stripes, total_tiles);
     return;
   }
+  if constexpr (Body::kProducerWarps == 4) asm volatile("setmaxnreg.inc.sync.aligned.u32 %0;" ::"n"(Body::kConsumerRegs));
 
   using Tile = std::conditional_t<Body::kLayout == kLayoutSymbol, SymTile<W, Body::kMaxOut, Body::kGroups>,
                                   PacketTile<W, Body::kMaxOut, Body::kGroups>>;
@@ -650,10 +698,26 @@ cudaError_t launch_body(const JobParams& p, const LaunchShape& sh, cudaStream_t 
   cudaError_t e = cudaGetDevice(&dev);
   if (e != cudaSuccess) return e;
   if (dev < 0 || dev >= kMaxDevices) return cudaErrorInvalidDevice;
-  if (sh.threads > (Body::kMaxWarps + 1) * 32) return cudaErrorInvalidConfiguration;
+  if (sh.threads > body_threads<Body>() || sh.threads % 32 || sh.threads / 32 <= Body::kProducerWarps)
+    return cudaErrorInvalidConfiguration;
+  if constexpr (Body::kProducerWarps == 4) {
+    // the producer warpgroup must start on a warpgroup boundary
+    if ((sh.threads / 32 - 4) % 4) return cudaErrorInvalidConfiguration;
+  }
   std::call_once(once[dev], [&] {
     attr_err[dev] = cudaFuncSetAttribute(rs_stripe_kernel<Body>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)kMaxDynamicSmem);
+    if constexpr (Body::kProducerWarps == 4) {
+      // setmaxnreg.inc draws on the registers the block was launched with:
+      // check that the compiled count covers the split (a shortfall would
+      // leave the consumers waiting for registers that never come)
+      cudaFuncAttributes fa;
+      cudaError_t e2 = cudaFuncGetAttributes(&fa, rs_stripe_kernel<Body>);
+      if (e2 == cudaSuccess && fa.numRegs * body_threads<Body>() <
+                                   Body::kProducerRegs * 128 + Body::kConsumerRegs * 32 * Body::kMaxWarps)
+        e2 = cudaErrorInvalidConfiguration;
+      if (attr_err[dev] == cudaSuccess) attr_err[dev] = e2;
+    }
   });
   if (attr_err[dev] != cudaSuccess) return attr_err[dev];
   rs_stripe_kernel<Body><<<sh.grid, sh.threads, sh.smem, st>>>(p);

@@ -125,6 +125,37 @@ def uniform01(words: np.ndarray) -> np.ndarray:
     return (words >> np.uint64(11)).astype(np.float64) * (1.0 / (1 << 53))
 
 
+MIXED_CODES = ((6, 3), (10, 4), (12, 4), (20, 4))
+
+
+def mixed_batch_shapes(seed: int, stripes: int = 4096, min_bytes: int = 4096, max_bytes: int = 8 << 20,
+                       decode_share: float = 0.30):
+    """Stripe shapes of the mixed batch: per stripe (k, m, B, e, offset).
+
+    (k, m) uniform over MIXED_CODES; B log-uniform on [min_bytes, max_bytes],
+    rounded down to a multiple of 4 KiB (at least 4 KiB); a decode with
+    probability decode_share, its erasure count e uniform in 1..m (e = 0:
+    an encode).  Stripe s draws words 4s .. 4s+3 of the shape sub-stream.
+    The stripes lie one after another in one buffer, each as k data blocks
+    then m parity blocks; `offset` is the stripe's first byte in it, and data
+    block j of stripe s holds the bytes offset + j*B .. of the data stream
+    (random_bytes(seed, offset + j*B, B)).
+    """
+    import math
+
+    u = uniform01(shape_draws(seed, 0, 4 * stripes)).reshape(stripes, 4)
+    out, off = [], 0
+    lo, hi = math.log(min_bytes), math.log(max_bytes)
+    for s in range(stripes):
+        k, m = MIXED_CODES[int(u[s, 0] * len(MIXED_CODES)) % len(MIXED_CODES)]
+        B = int(math.exp(lo + u[s, 1] * (hi - lo))) // 4096 * 4096
+        B = max(4096, B)
+        e = 1 + int(u[s, 3] * m) % m if u[s, 2] < decode_share else 0
+        out.append((k, m, B, e, off))
+        off += (k + m) * B
+    return out
+
+
 # ---------------------------------------------------------------- torch form
 def random_bytes_torch(seed: int, offset: int, nbytes: int, device="cpu"):
     """Same bytes as :func:`random_bytes`, generated with torch int64 ops.

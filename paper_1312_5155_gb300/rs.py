@@ -17,9 +17,11 @@ import threading
 PKG = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(PKG, "librs_gb300.so")
 
-RS_POLY, RS_VANDERMONDE, RS_CAUCHY, RS_POLY_MATRIX, RS_POLY_BITMATRIX = 0, 1, 2, 3, 4
+RS_POLY, RS_VANDERMONDE, RS_CAUCHY, RS_POLY_MATRIX, RS_POLY_BITMATRIX, RS_GOOD_CAUCHY = 0, 1, 2, 3, 4, 5
 REALIZATIONS = {"poly": RS_POLY, "vandermonde": RS_VANDERMONDE, "cauchy": RS_CAUCHY,
-                "poly_matrix": RS_POLY_MATRIX, "poly_bitmatrix": RS_POLY_BITMATRIX}
+                "poly_matrix": RS_POLY_MATRIX, "poly_bitmatrix": RS_POLY_BITMATRIX,
+                "good_cauchy": RS_GOOD_CAUCHY}
+PACKET_REALIZATIONS = ("cauchy", "poly_bitmatrix", "good_cauchy")
 RS_READ_MIN, RS_READ_ALL = 0, 1
 STATUS = {0: "RS_OK", 1: "RS_EINVAL", 2: "RS_ETOOMANY_ERASURES", 3: "RS_ENOMEM", 4: "RS_ECUDA",
           5: "RS_ETIMEOUT", 6: "RS_EUNSUPPORTED"}
@@ -71,7 +73,7 @@ def lib() -> ctypes.CDLL:
                 "rs_poly_encode_stripes_noalloc": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_int,
                                                                    ctypes.c_int, ctypes.POINTER(VP),
                                                                    ctypes.POINTER(VP),
-                                                                   ctypes.POINTER(ctypes.c_size_t), VP]),
+                                                                   ctypes.POINTER(ctypes.c_size_t), VP, VP]),
                 "rs_copy_blocks": (ctypes.c_int, [ctypes.POINTER(VP), ctypes.POINTER(VP),
                                                    ctypes.POINTER(ctypes.c_size_t), ctypes.c_int,
                                                    ctypes.c_size_t, VP]),
@@ -346,15 +348,18 @@ def rs_copy_blocks(dst, src, nbytes, stream=None, engine_min_bytes: int = 0) -> 
 
 
 # ------------------------------------------------- allocation-free encode
-def rs_poly_encode_stripes_noalloc(k: int, m: int, w: int, data, parity, block_bytes, stream=None) -> None:
+def rs_poly_encode_stripes_noalloc(k: int, m: int, w: int, data, parity, block_bytes, device_status=None,
+                                   stream=None) -> None:
     """Encode several polynomial RS(k, m) stripes without any device
-    allocation (for callers that cannot allocate: graph capture, allocator
-    callbacks, fixed memory budgets).  data: per stripe k device blocks;
-    parity: per stripe m device blocks; block_bytes: per stripe sizes."""
+    allocation, for callers that cannot allocate when they encode (allocator
+    callbacks, fixed device-memory budgets, paths that must not synchronise
+    the device).  data: per stripe k device blocks; parity: per stripe m
+    device blocks; block_bytes: per stripe sizes; device_status: None or a
+    zeroed int32 device tensor that receives a device-side wait timeout."""
     n = len(block_bytes)
     if len(data) != n or len(parity) != n:
         raise ValueError("data, parity and block_bytes need one entry per stripe")
     dp = _ptr_array([b for stripe in data for b in stripe])
     pp = _ptr_array([b for stripe in parity for b in stripe])
     bb = (ctypes.c_size_t * max(1, n))(*block_bytes)
-    _check(lib().rs_poly_encode_stripes_noalloc(k, m, w, n, dp, pp, bb, _stream(stream)))
+    _check(lib().rs_poly_encode_stripes_noalloc(k, m, w, n, dp, pp, bb, _ptr(device_status), _stream(stream)))

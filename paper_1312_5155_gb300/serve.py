@@ -214,6 +214,19 @@ class Server:
                     wait = pending[pi].arrival - (time.perf_counter() - t0)
                     if wait > 0:
                         time.sleep(min(wait, 0.001))
+        # a run cut short by time_limit: let the batches in flight finish and
+        # give back the memory of everything admitted (those requests count
+        # as complete only if their batch had finished)
+        for slot in self.slots:
+            if slot["reqs"] is not None:
+                slot["event"].synchronize()
+                tdone = time.perf_counter() - t0
+                for r in slot["reqs"]:
+                    r.done = tdone
+                    self.arena.release(r.off, r.size)
+                slot["reqs"] = None
+        for r in admitted:
+            self.arena.release(r.off, r.size)
         return requests
 
     def _launch(self, slot, reqs, payloads, results):
@@ -350,49 +363,87 @@ def make_results(requests, pool: "HostPool | None" = None):
     return {r.rid: pool.view(r.rid + 1, len(io_blocks(r)[1]), r.block_bytes) for r in requests}
 
 
-def saturation_rate(budget: int, pool: "HostPool", seconds: float = 2.0, seed: int = 0x5EED0005) -> float:
-    """Requests/s the batched server sustains when every request is already
-    waiting (all arrivals at t = 0)."""
+def drain_rate(budget: int, pool: "HostPool", seconds: float = 2.0, seed: int = 0x5EED0005, srv=None) -> float:
+    """Requests/s the batched server completes when every request is already
+    waiting (all arrivals at t = 0): an upper bound, since waiting requests
+    fill the largest batches."""
     reqs = make_requests(seed, 1e9, 1.0, max_requests=int(400 * seconds))
     for r in reqs:
         r.arrival = 0.0
     payloads = make_payloads(reqs, pool)
-    srv = Server(budget)
+    srv = srv or Server(budget)
     srv.run(reqs[:50], payloads)  # warm-up
     t0 = time.perf_counter()
     srv.run(reqs, payloads)
     dt = time.perf_counter() - t0
-    del srv
     return len(reqs) / dt
+
+
+def keeps_up(srv, pool, rate: float, seconds: float, p50_light_ms: float, seed: int = 0x5EED0006,
+             factor: float = 10.0):
+    """One Poisson run at `rate`: the server keeps up when every request
+    completes within 50 ms of the end of the arrivals and the p99 latency
+    stays within `factor` times the p50 latency at light load."""
+    reqs = make_requests(seed, rate, seconds)
+    payloads = make_payloads(reqs, pool)
+    srv.run(reqs, payloads)
+    s = summarize(reqs)
+    last = max((r.done for r in reqs), default=0.0)
+    ok = s.get("completed", 0) == len(reqs) and last <= seconds + 0.05 and s["p99_ms"] <= factor * p50_light_ms
+    return ok, s
+
+
+def saturation_rate(budget: int, pool: "HostPool", probe_seconds: float = 1.0, probes: int = 6,
+                    seed: int = 0x5EED0005) -> float:
+    """The highest Poisson arrival rate (requests/s) the batched server keeps
+    up with (keeps_up), found by bisection between 5 % and 100 % of the
+    drain rate.  Loads at or below it are sustained: p99 within a small
+    multiple (10x) of the light-load p50."""
+    srv = Server(budget)
+    top = drain_rate(budget, pool, seed=seed, srv=srv)
+    light = make_requests(seed + 1, 0.05 * top, probe_seconds)
+    srv.run(light, make_payloads(light, pool))
+    p50_light = summarize(light)["p50_ms"]
+    lo, hi = 0.05, 1.0
+    for _ in range(probes):
+        mid = 0.5 * (lo + hi)
+        ok, _ = keeps_up(srv, pool, mid * top, probe_seconds, p50_light)
+        if ok:
+            lo = mid
+        else:
+            hi = mid
+    del srv
+    return lo * top
 
 
 def main():
     ap = argparse.ArgumentParser(description=__doc__, formatter_class=argparse.RawDescriptionHelpFormatter)
     ap.add_argument("--budget-gib", type=float, default=32.0)
     ap.add_argument("--seconds", type=float, default=60.0)
-    ap.add_argument("--rates", default="0.1,0.5,0.9,1.2", help="fractions of the saturation rate")
+    ap.add_argument("--rates", default="0.1,0.3,0.5,0.7,0.9,1.0,1.2", help="fractions of the saturation rate")
     ap.add_argument("--streams", type=int, default=4)
     ap.add_argument("--serial", action="store_true", help="also run the serial per-request path")
     a = ap.parse_args()
     budget = int(a.budget_gib * (1 << 30))
     pool = HostPool(2 << 30)
     sat = saturation_rate(budget, pool)
-    out = {"saturation_req_per_s": sat, "runs": []}
+    out = {"saturation_req_per_s": sat, "seconds": a.seconds, "runs": []}
     srv = Server(budget, streams=a.streams)
+    codes = None
     for frac in [float(x) for x in a.rates.split(",")]:
         rate = frac * sat
         reqs = make_requests(inputs.workload_seed("serving"), rate, a.seconds)
         payloads = make_payloads(reqs, pool)
         results = make_results(reqs, pool)
-        srv.run(reqs, payloads, results)
-        row = {"rate_frac": frac, "rate": rate, "batched": summarize(reqs)}
+        srv.run(reqs, payloads, results, time_limit=a.seconds + 30.0)
+        row = {"rate_frac": frac, "rate": rate, "offered": len(reqs), "batched": summarize(reqs, wall=a.seconds)}
         if a.serial:
             import torch
             from . import rs
-            codes = {c: rs.Code(c[0], c[1], 8, "poly") for c in CODES}
+            codes = codes or {c: rs.Code(c[0], c[1], 8, "poly") for c in CODES}
             reqs2 = make_requests(inputs.workload_seed("serving"), rate, a.seconds)
-            serial_run(reqs2, payloads, results, codes, torch.device("cuda"), max_wall=2.0 * a.seconds)
-            row["serial"] = summarize(reqs2)
+            serial_run(reqs2, payloads, results, codes, torch.device("cuda"), max_wall=a.seconds + 10.0)
+            row["serial"] = summarize(reqs2, wall=a.seconds)
         out["runs"].append(row)
         print(json.dumps(row), flush=True)
     print(json.dumps(out))

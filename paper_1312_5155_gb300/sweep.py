@@ -10,17 +10,17 @@ Names:
             rs_encode / rs_decode call, and throughput of 1024 replicated
             stripes in one batched launch
   block_sizes  RS(6,3) and RS(10,4), GF(2^8), 1 GiB of data cut into stripes of
-            B = 4 KiB * 2^i (i = 0..14), poly / Vandermonde / Cauchy
-            (P = min(2 KiB, B/8)): batched encode, then batched decode with m
-            seeded erasures per stripe
+            B = 4 KiB * 2^i (i = 0..14), poly / Vandermonde / Cauchy / good
+            Cauchy (P = min(2 KiB, B/8)): batched encode, then batched decode
+            with m seeded erasures per stripe
   gf16_blocks  RS(12,4) GF(2^16) little-endian, 42 stripes of 4 MiB blocks:
-            poly and Cauchy encode, decode with e = 1..4
+            poly, Cauchy and good Cauchy encode, decode with e = 1..4
   mixed_batch  4096 stripes, (k, m) uniform over (6,3) (10,4) (12,4) (20,4),
             B log-uniform on [4 KiB, 8 MiB] (multiples of 4 KiB), 30 %
             decodes with e uniform in 1..m, poly: one batched launch set vs a
             loop of per-stripe rs_encode / rs_decode calls
   kmsweep   (k, 4) for k = 2..20 and (10, m) for m = 2..6, GF(2^8), 1 MiB
-            blocks, 1 GiB of data, all three realizations
+            blocks, 1 GiB of data, poly / Vandermonde / Cauchy / good Cauchy
   polyforms the polynomial code as LFSR, through its generator matrix and
             through that matrix's bit-matrix (packets), RS(10,4), RS(12,4),
             RS(6,3), 1 MiB blocks
@@ -80,7 +80,7 @@ def _fill(buf, seed, k, B, stripes):
 
 
 def _packet(real, w, B):
-    if real not in ("cauchy", "poly_bitmatrix"):
+    if real not in rs.PACKET_REALIZATIONS:
         return None
     return min(2048, B // w)
 
@@ -141,7 +141,7 @@ def single_stripe():
     print(json.dumps({"workload": "single_stripe", "what": "1024 replicated stripes, batched", **r}), flush=True)
 
 
-def block_sizes(blocks=None, codes=((6, 3), (10, 4)), reals=("poly", "vandermonde", "cauchy")):
+def block_sizes(blocks=None, codes=((6, 3), (10, 4)), reals=("poly", "vandermonde", "cauchy", "good_cauchy")):
     seed = inputs.workload_seed("block_sizes")
     for (k, m) in codes:
         for i in (blocks if blocks is not None else range(15)):
@@ -158,19 +158,22 @@ def gf16_blocks():
     k, m, w, B, stripes = 12, 4, 16, 4 << 20, 42
     seed = inputs.workload_seed("gf16_blocks")
     n = k + m
-    for real in ("poly", "cauchy"):
+    for real in ("poly", "cauchy", "good_cauchy"):
         buf = torch.empty((stripes, n, B), dtype=torch.uint8, device="cuda")
         _fill(buf, seed, k, B, stripes)
         code = rs.Code(k, m, w, real, packet_bytes=_packet(real, w, B))
         rows = [list(buf[s]) for s in range(stripes)]
         res = {}
+        sms = torch.cuda.get_device_properties(0).multi_processor_count
         b = rs.Batch(stripes)
-        b.set([(code, "encode", [], rows[s], B) for s in range(stripes)])
+        ops = [(code, "encode", [], rows[s], B) for s in range(stripes)]
+        shape, _ = autotune.tune_batch(b, ops, key=autotune.make_key(f"gf16-{stripes}-encode", real, k, m, w, B, sms))
         ms = _time(b.launch)
-        res["encode"] = {"ms": round(ms, 4), "gbs": round(stripes * n * B / ms / 1e6, 1)}
+        res["encode"] = {"ms": round(ms, 4), "gbs": round(stripes * n * B / ms / 1e6, 1), "shape": list(shape)}
         for e in range(1, m + 1):
             d = rs.Batch(stripes)
-            d.set([(code, "decode", inputs.erasure_pattern(seed, s, n, e), rows[s], B) for s in range(stripes)])
+            ops = [(code, "decode", inputs.erasure_pattern(seed, s, n, e), rows[s], B) for s in range(stripes)]
+            autotune.tune_batch(d, ops, key=autotune.make_key(f"gf16-{stripes}-decode{e}", real, k, m, w, B, sms))
             ms = _time(d.launch)
             if d.poll_status() != 0:
                 raise RuntimeError("device status set")
@@ -182,68 +185,118 @@ def gf16_blocks():
         torch.cuda.empty_cache()
 
 
+def _graph_of(launch):
+    """A CUDA graph holding one call of `launch` (captured on a side stream
+    after a warm-up call outside the capture)."""
+    torch = _torch()
+    s = torch.cuda.Stream()
+    s.wait_stream(torch.cuda.current_stream())
+    with torch.cuda.stream(s):
+        launch()
+        torch.cuda.synchronize()
+        g = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(g, stream=s):
+            launch()
+    torch.cuda.current_stream().wait_stream(s)
+    torch.cuda.synchronize()
+    return g
+
+
+def _percentile(xs, q):
+    xs = sorted(xs)
+    return xs[min(len(xs) - 1, max(0, int(math.ceil(q * len(xs))) - 1))]
+
+
 def mixed_batch(stripes=4096, reps=5):
+    """Config-4 batch: all stripes submitted at once.  Batched form = the
+    persistent launches of one rs_batch, captured once in a CUDA graph and
+    replayed; per-stripe form = one rs_encode / rs_decode call per stripe on
+    the same stream.  Per-op latency = completion time of the op measured
+    from the submission of the whole batch (batched: the end of the graph
+    replay, which completes every op; loop: a CUDA event after each call)."""
     torch = _torch()
     seed = inputs.workload_seed("mixed_batch")
-    codes = [(6, 3), (10, 4), (12, 4), (20, 4)]
-    u = inputs.uniform01(inputs.shape_draws(seed, 0, 4 * stripes)).reshape(stripes, 4)
-    shapes = []
-    for s in range(stripes):
-        k, m = codes[int(u[s, 0] * 4) % 4]
-        B = int(math.exp(math.log(4096) + u[s, 1] * (math.log(8 << 20) - math.log(4096)))) // 4096 * 4096
-        B = max(4096, B)
-        dec = u[s, 2] < 0.30
-        e = 1 + int(u[s, 3] * m) % m if dec else 0
-        shapes.append((k, m, B, e))
-    total = sum((k + m) * B for k, m, B, _ in shapes)
+    shapes = inputs.mixed_batch_shapes(seed, stripes)
+    total = sum((k + m) * B for k, m, B, _, _ in shapes)
     arena = torch.empty(total, dtype=torch.uint8, device="cuda")
-    code = {c: rs.Code(c[0], c[1], 8, "poly") for c in codes}
-    views, off = [], 0
-    for s, (k, m, B, e) in enumerate(shapes):
+    code = {c: rs.Code(c[0], c[1], 8, "poly") for c in inputs.MIXED_CODES}
+    views = []
+    for s, (k, m, B, e, off) in enumerate(shapes):
         v = arena[off:off + (k + m) * B].view(k + m, B)
         v[:k] = inputs.random_bytes_torch(seed, off, k * B, "cuda").view(k, B)
         views.append(v)
-        off += (k + m) * B
     torch.cuda.synchronize()
     # valid parity first so the decodes rebuild real codewords
     enc_all = rs.Batch(stripes)
-    enc_all.set([(code[(k, m)], "encode", [], list(views[s]), B) for s, (k, m, B, e) in enumerate(shapes)])
+    enc_all.set([(code[(k, m)], "encode", [], list(views[s]), B) for s, (k, m, B, e, _) in enumerate(shapes)])
     enc_all.launch()
     torch.cuda.synchronize()
-    ops = []
-    for s, (k, m, B, e) in enumerate(shapes):
-        if e:
-            ops.append((code[(k, m)], "decode", inputs.erasure_pattern(seed, s, k + m, e), list(views[s]), B))
-        else:
-            ops.append((code[(k, m)], "encode", [], list(views[s]), B))
-    nbytes = sum((k + m) * B if not e else (k + e) * B for k, m, B, e in shapes)
+    ops = mixed_batch_ops(seed, shapes, views, code)
+    nbytes = sum((k + m) * B if not e else (k + e) * B for k, m, B, e, _ in shapes)
     b = rs.Batch(stripes)
     sms = torch.cuda.get_device_properties(0).multi_processor_count
-    autotune.tune_batch(b, ops, key=autotune.make_key(f"mixed_batch-{stripes}", "poly-mixed", 0, 0, 8, 1 << 20, sms))
+    shape, _ = autotune.tune_batch(b, ops, key=autotune.make_key(f"mixed_batch-{stripes}", "poly-mixed", 0, 0, 8,
+                                                                  1 << 20, sms))
     ms_batch = _time(b.launch, reps=reps, warm=2)
+    g = _graph_of(b.launch)
+    ms_graph = _time(g.replay, reps=reps, warm=2)
     if b.poll_status() != 0:
         raise RuntimeError("device status set")
     # the same ops as a loop of per-stripe calls on one stream
     calls = []
     for c, op, er, rows, B in ops:
         if op == "encode":
-            k = c.k
-            calls.append((c.encode, (rows[:k], rows[k:], B)))
+            calls.append((c.encode, (rows[:c.k], rows[c.k:], B)))
         else:
             calls.append((c.decode, (er, rows, B)))
 
-    def loop():
-        for f, a in calls:
+    def loop(evs=None):
+        for i, (f, a) in enumerate(calls):
             f(*a)
+            if evs is not None:
+                evs[i].record()
 
     ms_loop = _time(loop, reps=reps, warm=1)
-    print(json.dumps({"workload": "mixed_batch", "stripes": stripes, "bytes": nbytes, "gib_resident": round(total / GIB, 2),
-                      "decodes": sum(1 for x in shapes if x[3]), "kernel_launches_batched": b.kernel_count,
+    t0 = torch.cuda.Event(enable_timing=True)
+    evs = [torch.cuda.Event(enable_timing=True) for _ in calls]
+    t0.record()
+    loop(evs)
+    torch.cuda.synchronize()
+    lat_loop = [t0.elapsed_time(e) for e in evs]
+    lat_graph = []
+    for _ in range(reps):
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record()
+        g.replay()
+        e1.record()
+        torch.cuda.synchronize()
+        lat_graph.append(e0.elapsed_time(e1))
+    print(json.dumps({"workload": "mixed_batch", "stripes": stripes, "bytes": nbytes,
+                      "gib_resident": round(total / GIB, 2), "decodes": sum(1 for x in shapes if x[3]),
+                      "kernel_launches_batched": b.kernel_count, "launch_shape": list(shape),
                       "batched": {"ms": round(ms_batch, 3), "gbs": round(nbytes / ms_batch / 1e6, 1)},
-                      "per_stripe_loop": {"ms": round(ms_loop, 3), "gbs": round(nbytes / ms_loop / 1e6, 1)}}),
+                      "graph_replay": {"ms": round(ms_graph, 3), "gbs": round(nbytes / ms_graph / 1e6, 1),
+                                       "op_latency_p50_ms": round(statistics.median(lat_graph), 3),
+                                       "op_latency_p99_ms": round(max(lat_graph), 3)},
+                      "per_stripe_loop": {"ms": round(ms_loop, 3), "gbs": round(nbytes / ms_loop / 1e6, 1),
+                                          "op_latency_p50_ms": round(_percentile(lat_loop, 0.5), 3),
+                                          "op_latency_p99_ms": round(_percentile(lat_loop, 0.99), 3)}}),
           flush=True)
     b.close()
     enc_all.close()
+
+
+def mixed_batch_ops(seed, shapes, views, code):
+    """The batch's ops: stripe s is decoded (erasure pattern of stripe s, e
+    blocks) when its shape has e > 0, else encoded."""
+    ops = []
+    for s, (k, m, B, e, _) in enumerate(shapes):
+        if e:
+            ops.append((code[(k, m)], "decode", inputs.erasure_pattern(seed, s, k + m, e), list(views[s]), B))
+        else:
+            ops.append((code[(k, m)], "encode", [], list(views[s]), B))
+    return ops
 
 
 def kmsweep():
@@ -251,7 +304,7 @@ def kmsweep():
     B = 1 << 20
     for (k, m) in [(k, 4) for k in range(2, 21)] + [(10, m) for m in (2, 3, 5, 6)]:
         stripes = max(1, GIB // (k * B))
-        for real in ("poly", "vandermonde", "cauchy"):
+        for real in ("poly", "vandermonde", "cauchy", "good_cauchy"):
             r = _batch_pair(real, 8, k, m, B, stripes, seed, m, tag="km-")
             print(json.dumps({"sweep": "km", "k": k, "m": m, "B": B, "stripes": stripes, "realization": real,
                               **r}), flush=True)

@@ -121,7 +121,7 @@ void run_decode2(const DecodePlan& pl, uint8_t* blocks, size_t B) {
   for (size_t seg = 0; seg < B; seg += segb)
     for (int lane = 0; lane < 32; ++lane) {
       HostTileG<W, 2> t{in.data(), out.data(), B, seg, lane};
-      PolyDecode2<W, M>::run(pl.n_pos, pl.read_mask, pl.e, t, t, cf);
+      PolyDecode2<W, M, true>::run(pl.n_pos, pl.read_mask, pl.e, t, t, cf);  // pair sums, as the kernel
     }
 }
 
@@ -302,7 +302,7 @@ int mat_fixed2_packet(const DecodePlan* pl, uint8_t* blocks, size_t B, size_t P)
   for (size_t sp = 0; sp < B; sp += (size_t)W * P)
     for (size_t u = 0; u < P / 8; ++u) {
       HostPacketTile2<W> t{in.data(), out.data(), sp, P, u};
-      MatDecodeFixed2<W, K, M, KIND, false>::run(pl->read_mask, pl->e, t, t, cf);
+      MatDecodeFixed2<W, K, M, KIND, false, true>::run(pl->read_mask, pl->e, t, t, cf);  // pair sums, as the kernel
     }
   return 0;
 }
@@ -340,7 +340,7 @@ int mat_runtime_m(int k, int m, const std::vector<uint32_t>& P, bool decode, con
 
 template <int KIND>
 int mat_fixed_dispatch(int w, int k, int m, bool decode, const DecodePlan* pl, uint8_t* b, size_t B, size_t pkt) {
-  if (KIND >= 3) {
+  if (KIND == 3 || KIND == 4) {
     if (w == 8 && k == 10 && m == 4) return mat_fixed<8, 10, 4, KIND>(decode, pl, b, B, pkt);
     if (w == 8 && k == 6 && m == 3) return mat_fixed<8, 6, 3, KIND>(decode, pl, b, B, pkt);
     if (w == 16 && k == 12 && m == 4) return mat_fixed<16, 12, 4, KIND>(decode, pl, b, B, pkt);
@@ -439,6 +439,7 @@ long emu_packet_tiles(int w, int groups, uint32_t P, int nc, int nsp, int whole_
 static bool host_parity(int w, int k, int m, int kind, std::vector<uint32_t>& P) {
   if (kind == 1) return vandermonde_parity_matrix(k, m, w, P);
   if (kind == 2) cauchy_parity_matrix(k, m, w, P);
+  else if (kind == 5) good_cauchy_parity_matrix(k, m, w, P);
   else poly_parity_matrix(k, m, w, P);
   return true;
 }
@@ -460,10 +461,11 @@ int emu_mat(int w, int k, int m, int kind, int fixed, const int* er, int e, int 
       case 2: return mat_fixed_dispatch<2>(w, k, m, decode, plp, blocks, B, pkt);
       case 3: return mat_fixed_dispatch<3>(w, k, m, decode, plp, blocks, B, pkt);
       case 4: return mat_fixed_dispatch<4>(w, k, m, decode, plp, blocks, B, pkt);
+      case 5: return mat_fixed_dispatch<5>(w, k, m, decode, plp, blocks, B, pkt);
     }
     return -2;
   }
-  const bool packet = kind == 2 || kind == 4;
+  const bool packet = kind == 2 || kind == 4 || kind == 5;
   if (w == 8) return packet ? mat_runtime_m<8, true>(k, m, P, decode, plp, blocks, B, pkt)
                             : mat_runtime_m<8, false>(k, m, P, decode, plp, blocks, B, pkt);
   return packet ? mat_runtime_m<16, true>(k, m, P, decode, plp, blocks, B, pkt)
@@ -494,7 +496,7 @@ int emu_mat_decode2(int w, int k, int m, int kind, const int* er, int e, int rea
 // 4; P = packet bytes, a multiple of 8 dividing B / 8).
 int emu_mat_decode2_packet(int w, int k, int m, int kind, const int* er, int e, int read_all, uint8_t* blocks,
                            size_t B, size_t P) {
-  if (w != 8 || (kind != 2 && kind != 4) || e <= 0 || P % 8 || B % (8 * P)) return -2;
+  if (w != 8 || (kind != 2 && kind != 4 && kind != 5) || e <= 0 || P % 8 || B % (8 * P)) return -2;
   std::vector<uint32_t> Pm;
   if (!host_parity(w, k, m, kind, Pm)) return -3;
   DecodePlan pl;
@@ -504,6 +506,9 @@ int emu_mat_decode2_packet(int w, int k, int m, int kind, const int* er, int e, 
   if (kind == 2) {
     if (k == 10 && m == 4) return mat_fixed2_packet<8, 10, 4, 2>(&pl, blocks, B, P);
     if (k == 6 && m == 3) return mat_fixed2_packet<8, 6, 3, 2>(&pl, blocks, B, P);
+  } else if (kind == 5) {
+    if (k == 10 && m == 4) return mat_fixed2_packet<8, 10, 4, 5>(&pl, blocks, B, P);
+    if (k == 6 && m == 3) return mat_fixed2_packet<8, 6, 3, 5>(&pl, blocks, B, P);
   } else {
     if (k == 10 && m == 4) return mat_fixed2_packet<8, 10, 4, 4>(&pl, blocks, B, P);
   }
@@ -525,19 +530,20 @@ int emu_fixed_parity_matrix(int w, int k, int m, int kind, uint32_t* out) {
       for (int j = 0; j < K; ++j) out[i * K + j] = mat.a[i][j];
     return 0;
   };
-  if (kind == 3) {
-    if (w == 8 && k == 10 && m == 4) return copy(ParityMatrix<8, 10, 4, 3>::value, 10, 4);
-    if (w == 16 && k == 12 && m == 4) return copy(ParityMatrix<16, 12, 4, 3>::value, 12, 4);
-    return -2;
+  // every (w, k, m) the library compiles matrix kernels for, each kind
+#define RSGB_EMU_FIXED(W, K, M)                                                            \
+  if (w == W && k == K && m == M) {                                                         \
+    if (kind == 1) return copy(ParityMatrix<W, K, M, 1>::value, K, M);                      \
+    if (kind == 2) return copy(ParityMatrix<W, K, M, 2>::value, K, M);                      \
+    if (kind == 3) return copy(ParityMatrix<W, K, M, 3>::value, K, M);                      \
+    if (kind == 5) return copy(ParityMatrix<W, K, M, 5>::value, K, M);                      \
   }
-  if (kind == 1) {
-    if (w == 8 && k == 10 && m == 4) return copy(ParityMatrix<8, 10, 4, 1>::value, 10, 4);
-    if (w == 8 && k == 20 && m == 4) return copy(ParityMatrix<8, 20, 4, 1>::value, 20, 4);
-    if (w == 16 && k == 12 && m == 4) return copy(ParityMatrix<16, 12, 4, 1>::value, 12, 4);
-  } else {
-    if (w == 8 && k == 10 && m == 4) return copy(ParityMatrix<8, 10, 4, 2>::value, 10, 4);
-    if (w == 16 && k == 12 && m == 4) return copy(ParityMatrix<16, 12, 4, 2>::value, 12, 4);
-  }
+  RSGB_EMU_FIXED(8, 6, 3)
+  RSGB_EMU_FIXED(8, 10, 4)
+  RSGB_EMU_FIXED(8, 12, 4)
+  RSGB_EMU_FIXED(8, 20, 4)
+  RSGB_EMU_FIXED(16, 12, 4)
+#undef RSGB_EMU_FIXED
   return -2;
 }
 

@@ -50,3 +50,10 @@ def test_argument_errors_need_no_gpu(library):
     assert L.rs_init(10, 4, 8, 9, ctypes.byref(h)) == 1  # realization
     assert L.rs_encode(None, None, None, 0, None) == 1
     assert L.rs_version() >= 100
+
+
+def test_generated_select_header_is_current():
+    """csrc/select_gen.hpp is exactly what gen_select.py renders."""
+    from paper_1312_5155_gb300 import gen_select
+    with open(gen_select.OUT) as f:
+        assert f.read() == gen_select.render()

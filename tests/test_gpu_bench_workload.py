@@ -1,12 +1,12 @@
 """GPU parity at the benchmark's full size: the RS(10,4) workload of 1 GiB of
-data in 102 stripes of 10 x 1 MiB blocks, in all three realizations, run
+data in 102 stripes of 10 x 1 MiB blocks, in all four realizations, run
 through the same batches, launch shapes (autotuned) and erasure patterns that
 bench.py times.
 
-The oracle cannot redo 3 x 1.4 GiB in test time, so it checks samples:
+The oracle cannot redo 4 x 1.4 GiB in test time, so it checks samples:
 every stripe on 64 random byte columns (in the symbol layout each byte
 offset is a codeword of its own) or on one random super-packet (in the
-Cauchy packet layout the super-packets are independent), and three whole
+Cauchy packet layouts the super-packets are independent), and three whole
 stripes per realization.  The check runs after the decode, on all 14
 blocks: the rebuilt blocks must equal the original data and parity, and
 the blocks left alone must hold the batched encode's parity."""
@@ -54,7 +54,7 @@ def test_bench_workload_sampled_parity():
     for s in range(wl.S):
         data = inputs.random_bytes(seed, bench.global_stripe(0, s, wl.S) * K * B, K * B).reshape(K, B)
         for real in bench.REALIZATIONS:
-            if real == "cauchy":
+            if real in bench.PACKET_REALIZATIONS:
                 sp = int(rng.integers(0, B // (W * P)))
                 sel = slice(sp * W * P, (sp + 1) * W * P)
                 ref = np.zeros((K + M, W * P), dtype=np.uint8)

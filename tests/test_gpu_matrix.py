@@ -1,5 +1,6 @@
 """GPU parity: Vandermonde (symbol layout) and Cauchy bit-matrix (packet
-layout) realizations through the C ABI vs the CPU oracle, bit-exact.
+layout; original and "good" Cauchy matrices) realizations through the C ABI
+vs the CPU oracle, bit-exact.
 Registered codes run the compile-time-generator kernels, other codes the
 runtime-generator kernels; both are covered."""
 import numpy as np
@@ -45,6 +46,11 @@ CASES = [
     ("poly_matrix", 16, 12, 4, 100002, None), ("poly_matrix", 8, 7, 5, 50000, None),
     ("poly_bitmatrix", 8, 10, 4, 8 * 2048 * 8, 2048), ("poly_bitmatrix", 8, 6, 3, 8 * 1024 * 3, 1024),
     ("poly_bitmatrix", 16, 12, 4, 16 * 2048 * 2, 2048),
+    # good Cauchy (GoodCRS): compiled codes, two-group decodes, runtime-P codes
+    ("good_cauchy", 8, 10, 4, 8 * 2048 * 8, 2048), ("good_cauchy", 8, 6, 3, 8 * 2048 * 3, 2048),
+    ("good_cauchy", 16, 12, 4, 16 * 2048 * 2, 2048), ("good_cauchy", 8, 10, 4, 8 * 512 * 5, 512),
+    ("good_cauchy", 8, 7, 5, 8 * 1024 * 3, 1024), ("good_cauchy", 8, 20, 4, 8 * 384 * 2, 384),
+    ("good_cauchy", 8, 12, 4, 8 * 2048 * 4, 2048), ("good_cauchy", 16, 3, 2, 16 * 128 * 4, 128),
 ]
 
 
@@ -114,7 +120,7 @@ def test_cauchy_block_size_must_fit_packets(rs):
 @pytest.mark.parametrize("real,w,k,m,pkt,nsp", [("cauchy", 8, 10, 4, 2048, 7), ("cauchy", 8, 10, 4, 256, 37),
                                                 ("cauchy", 8, 10, 4, 768, 5), ("cauchy", 8, 7, 5, 640, 9),
                                                 ("poly_bitmatrix", 8, 10, 4, 1024, 6),
-                                                ("cauchy", 16, 12, 4, 384, 5)])
+                                                ("cauchy", 16, 12, 4, 384, 5), ("good_cauchy", 8, 10, 4, 768, 5)])
 def test_packet_tiles_any_warp_count(rs, real, w, k, m, pkt, nsp, warps):
     import torch
     B = nsp * w * pkt
@@ -138,3 +144,20 @@ def test_packet_tiles_any_warp_count(rs, real, w, k, m, pkt, nsp, warps):
         torch.cuda.synchronize()
         assert np.array_equal(to_host(buf, B), ref), er
     assert code.poll_status() == 0
+
+
+def test_good_cauchy_has_fewer_ones_and_differs_from_cauchy(rs):
+    """The good Cauchy code is a different code (other parity bytes) whose
+    bit-matrix has fewer ones than the original's (the XOR count)."""
+    import torch
+    w, k, m, pkt = 8, 10, 4, 2048
+    B = 8 * pkt * 4
+    ones = lambda C: sum(O.bitmatrix_ones(w, int(x)) for x in C.ravel())
+    assert ones(O.goodcauchy_matrix(w, k, m)) < ones(O.cauchy_matrix(w, k, m))
+    host = stripe(w, k, m, B)
+    a_buf, a_rows = device_blocks(host)
+    b_buf, b_rows = device_blocks(host)
+    rs.Code(k, m, w, "cauchy", packet_bytes=pkt).encode(a_rows[:k], a_rows[k:], B)
+    rs.Code(k, m, w, "good_cauchy", packet_bytes=pkt).encode(b_rows[:k], b_rows[k:], B)
+    torch.cuda.synchronize()
+    assert torch.equal(a_buf[:k], b_buf[:k]) and not torch.equal(a_buf[k:], b_buf[k:])

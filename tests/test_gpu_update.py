@@ -25,6 +25,7 @@ def rs():
 CASES = [("poly", 8, 10, 4, (1 << 20) + 48, None), ("poly", 8, 6, 3, 5000, None), ("poly", 16, 12, 4, 40002, None),
          ("poly", 8, 20, 8, 70000, None), ("vandermonde", 8, 10, 4, 65536 + 16, None),
          ("cauchy", 8, 10, 4, 8 * 2048 * 4, 2048), ("cauchy", 16, 6, 3, 16 * 512 * 2, 512),
+         ("good_cauchy", 8, 10, 4, 8 * 2048 * 4, 2048),
          ("poly_matrix", 8, 7, 5, 30000, None), ("poly_bitmatrix", 8, 10, 4, 8 * 1024 * 3, 1024)]
 
 

@@ -12,7 +12,7 @@ from paper_1312_5155_gb300 import inputs
 from tests.hostemu.build import build
 
 U8P = ctypes.POINTER(ctypes.c_uint8)
-KIND = {"vandermonde": 1, "cauchy": 2, "poly_matrix": 3, "poly_bitmatrix": 4}
+KIND = {"vandermonde": 1, "cauchy": 2, "poly_matrix": 3, "poly_bitmatrix": 4, "good_cauchy": 5}
 FIXED = {(8, 6, 3), (8, 10, 4), (8, 12, 4), (8, 20, 4), (16, 12, 4)}
 FIXED_POLY = {(8, 10, 4), (8, 6, 3), (16, 12, 4)}  # harness instantiations of kinds 3 and 4
 
@@ -39,10 +39,12 @@ def oracle_parity(real, w, k, m):
         return O.vand_matrix(w, k, m)[k:]
     if real == "cauchy":
         return O.cauchy_matrix(w, k, m)
+    if real == "good_cauchy":
+        return O.goodcauchy_matrix(w, k, m)
     return O.polymat_matrix(w, k, m)
 
 
-@pytest.mark.parametrize("real", ["vandermonde", "cauchy", "poly_matrix"])
+@pytest.mark.parametrize("real", ["vandermonde", "cauchy", "poly_matrix", "good_cauchy"])
 @pytest.mark.parametrize("w,k,m", [(8, 10, 4), (8, 6, 3), (16, 12, 4), (8, 5, 7), (8, 20, 4), (16, 3, 2)])
 def test_host_parity_matrix_matches_oracle(emu, real, w, k, m):
     out = (ctypes.c_uint32 * (k * m))()
@@ -51,13 +53,13 @@ def test_host_parity_matrix_matches_oracle(emu, real, w, k, m):
     assert np.array_equal(got, oracle_parity(real, w, k, m))
 
 
-@pytest.mark.parametrize("real", ["vandermonde", "cauchy", "poly_matrix"])
-@pytest.mark.parametrize("w,k,m", [(8, 10, 4), (16, 12, 4), (8, 20, 4)])
+@pytest.mark.parametrize("real", ["vandermonde", "cauchy", "poly_matrix", "good_cauchy"])
+@pytest.mark.parametrize("w,k,m", [(8, 6, 3), (8, 10, 4), (8, 12, 4), (8, 20, 4), (16, 12, 4)])
 def test_compile_time_parity_matrix_matches_oracle(emu, real, w, k, m):
+    """The compile-time (constexpr) generators the fixed-code kernels are
+    built from equal the oracle's matrices for every compiled code."""
     out = (ctypes.c_uint32 * (k * m))()
-    rc = emu.emu_fixed_parity_matrix(w, k, m, KIND[real], out)
-    if rc == -2:
-        pytest.skip("not exported by the harness")
+    assert emu.emu_fixed_parity_matrix(w, k, m, KIND[real], out) == 0
     got = np.array(list(out), dtype=np.uint32).reshape(m, k)
     assert np.array_equal(got, oracle_parity(real, w, k, m))
 
@@ -77,7 +79,10 @@ CASES = [("vandermonde", 8, 10, 4, 4096 + 48, 0), ("vandermonde", 8, 6, 3, 3000,
          ("poly_matrix", 8, 10, 4, 4096 + 48, 0), ("poly_matrix", 8, 6, 3, 3000, 0),
          ("poly_matrix", 16, 12, 4, 8192 + 2, 0), ("poly_matrix", 8, 5, 7, 2048, 0),
          ("poly_bitmatrix", 8, 10, 4, 8 * 256 * 2, 256), ("poly_bitmatrix", 8, 6, 3, 8 * 128 * 3, 128),
-         ("poly_bitmatrix", 16, 12, 4, 16 * 128 * 2, 128), ("poly_bitmatrix", 8, 5, 7, 8 * 384, 384)]
+         ("poly_bitmatrix", 16, 12, 4, 16 * 128 * 2, 128), ("poly_bitmatrix", 8, 5, 7, 8 * 384, 384),
+         ("good_cauchy", 8, 10, 4, 8 * 256 * 2, 256), ("good_cauchy", 8, 6, 3, 8 * 128 * 3, 128),
+         ("good_cauchy", 16, 12, 4, 16 * 128 * 2, 128), ("good_cauchy", 8, 5, 7, 8 * 384, 384),
+         ("good_cauchy", 8, 20, 4, 8 * 128, 128)]
 
 
 def fixed_ok(real, w, k, m):
@@ -116,7 +121,7 @@ def test_decode_seeded_patterns(emu, real, w, k, m, B, pkt, read_all):
             assert np.array_equal(got, base), (er, fixed)
 
 
-@pytest.mark.parametrize("real", ["vandermonde", "cauchy", "poly_matrix", "poly_bitmatrix"])
+@pytest.mark.parametrize("real", ["vandermonde", "cauchy", "poly_matrix", "poly_bitmatrix", "good_cauchy"])
 def test_decode_every_pattern_rs_6_3(emu, real):
     w, k, m = 8, 6, 3
     pkt = 128
@@ -159,7 +164,8 @@ def test_two_group_matrix_decode_matches_oracle(emu, real, k, m, B, read_all):
 
 @pytest.mark.parametrize("read_all", [False, True])
 @pytest.mark.parametrize("real,k,m,pkt,sp", [("cauchy", 10, 4, 256, 3), ("cauchy", 6, 3, 2048, 1),
-                                             ("poly_bitmatrix", 10, 4, 512, 2)])
+                                             ("poly_bitmatrix", 10, 4, 512, 2), ("good_cauchy", 10, 4, 256, 3),
+                                             ("good_cauchy", 6, 3, 2048, 1)])
 def test_two_group_packet_decode_matches_oracle(emu, real, k, m, pkt, sp, read_all):
     """The packet-layout compile-time-P decode with two adjacent words per
     thread (one 64-bit load per packet row)."""

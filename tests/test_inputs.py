@@ -46,3 +46,24 @@ def test_stripe_blocks_layout():
     assert np.array_equal(s.ravel(), flat)
     win = inputs.stripe_blocks(9, 2, k, B, col0=4, ncols=3)
     assert np.array_equal(win, s[:, 4:7])
+
+
+def test_mixed_batch_shapes_follow_the_recipe():
+    shapes = inputs.mixed_batch_shapes(inputs.workload_seed("mixed_batch"), 4096)
+    assert len(shapes) == 4096
+    off = 0
+    codes = set()
+    for k, m, B, e, o in shapes:
+        assert (k, m) in inputs.MIXED_CODES
+        assert 4096 <= B <= 8 << 20 and B % 4096 == 0
+        assert 0 <= e <= m
+        assert o == off
+        off += (k + m) * B
+        codes.add((k, m))
+    assert codes == set(inputs.MIXED_CODES)
+    dec = sum(1 for s in shapes if s[3])
+    assert 0.25 < dec / 4096 < 0.35
+    # log-uniform sizes: the median is near the geometric mean of the range
+    med = sorted(s[2] for s in shapes)[2048]
+    assert 100 << 10 < med < 300 << 10
+    assert shapes[:10] == inputs.mixed_batch_shapes(inputs.workload_seed("mixed_batch"), 10)
