@@ -512,7 +512,8 @@ def run_serve():
     highest rate it keeps up with, found by bisection), request latency
     p50 / p99 and served GB/s; then the batched server and the serial
     per-request path at the same offered rate, half of what the serial path
-    sustains."""
+    sustains, and at twice that capacity (the serial path falls behind:
+    fewer requests completed within the run, lower GB/s)."""
     from paper_1312_5155_gb300 import inputs, rs, serve
 
     budget = 32 << 30
@@ -535,6 +536,16 @@ def run_serve():
     reqs_s = serve.make_requests(inputs.workload_seed("serving"), srate, SERVE_SECONDS)
     serve.serial_run(reqs_s, pay_b, res_b, codes, __import__("torch").device("cuda"),
                      max_wall=SERVE_SECONDS + 5.0)
+    # past the serial path's capacity (and below the batched saturation):
+    # the batched server keeps up, the serial path falls behind
+    orate = min(2.0 * cap, 0.8 * sat)
+    over_s = 2.0
+    reqs_ob = serve.make_requests(inputs.workload_seed("serving") + 11, orate, over_s)
+    pay_o = serve.make_payloads(reqs_ob, pool)
+    res_o = serve.make_results(reqs_ob, pool)
+    srv.run(reqs_ob, pay_o, res_o)
+    reqs_os = serve.make_requests(inputs.workload_seed("serving") + 11, orate, over_s)
+    serve.serial_run(reqs_os, pay_o, res_o, codes, __import__("torch").device("cuda"), max_wall=over_s)
     del srv
 
     def rnd(d):
@@ -544,7 +555,10 @@ def run_serve():
             "seconds": SERVE_SECONDS, "requests": len(reqs), **rnd(summary),
             "vs_serial": {"rate_req_per_s": round(srate, 1), "serial_capacity_req_per_s": round(cap, 1),
                           "requests": len(reqs_b), "batched": rnd(serve.summarize(reqs_b, wall=SERVE_SECONDS)),
-                          "serial": rnd(serve.summarize(reqs_s, wall=SERVE_SECONDS))}}
+                          "serial": rnd(serve.summarize(reqs_s, wall=SERVE_SECONDS))},
+            "overload": {"rate_req_per_s": round(orate, 1), "seconds": over_s, "requests": len(reqs_ob),
+                         "batched": rnd(serve.summarize(reqs_ob, wall=over_s)),
+                         "serial": rnd(serve.summarize(reqs_os, wall=over_s))}}
 
 
 # ------------------------------------------------------------ oracle arm

@@ -36,6 +36,18 @@ NVCC_FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC,-O2",
 # Kinds: 1 Vandermonde, 2 Cauchy, 3 / 4 the polynomial code's generator
 # matrix (symbol / packet layout), 5 good Cauchy.
 FIXED_CODES = [(8, 6, 3), (8, 10, 4), (8, 12, 4), (8, 20, 4), (16, 12, 4)]
+# Every code of the paper's k and m studies (§5.2 Fig. 3: (k, 4), k = 2..20;
+# Fig. 4: (10, m), m = 2..6), compiled in addition when the environment sets
+# RSGB_BUILD_KM_CODES=1 (about 200 more units: a longer build, used for the
+# k/m sweep so that every realization runs a compiled generator).
+KM_CODES = [(8, k, 4) for k in range(2, 21)] + [(8, 10, m) for m in (2, 3, 5, 6)]
+
+
+def fixed_codes() -> list:
+    codes = list(FIXED_CODES)
+    if os.environ.get("RSGB_BUILD_KM_CODES") == "1":
+        codes += [c for c in KM_CODES if c not in codes]
+    return codes
 # compile-time generator-matrix forms of the polynomial code
 FIXED_POLY_MATRIX_CODES = [(8, 10, 4)]
 MIXED_POLY = [(8, (3, 4))]
@@ -63,7 +75,7 @@ def instances():
                 for layout in (0, 1):
                     out.append((f"matrt_w{w}_m{m}_op{op}_l{layout}", f"MatRuntimeBody<{w}, {m}, {op}, {layout}>",
                                 dict(family=1, w=w, m=m, op=op, layout=layout)))
-    fixed = [(c, kind) for c in FIXED_CODES for kind in (1, 2, 5)] + \
+    fixed = [(c, kind) for c in fixed_codes() for kind in (1, 2, 5)] + \
         [(c, kind) for c in FIXED_POLY_MATRIX_CODES for kind in (3, 4)]
     for (w, k, m), kind in fixed:
         for op in (2, 3):

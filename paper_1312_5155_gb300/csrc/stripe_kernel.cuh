@@ -343,8 +343,16 @@ RS_CHD constexpr int body_min_blocks(int w, int max_warps, int live_words) {
   return (w == 8 && max_warps <= 8 && live_words <= 64) ? 2 : 1;
 }
 
+// One-group GF(2^8) decodes that keep more than four syndromes (two
+// selector chunks, 122-141 registers at m = 5, 6) get 12 consumer warps
+// from the split instead of 8.
 template <int W, int M, int OP>
-struct PolyBody : std::conditional_t<W == 16 && OP == kOpDecode, Wide16DecodeSplit, NoSplit> {
+using PolyBodySplit =
+    std::conditional_t<OP == kOpDecode && W == 16, Wide16DecodeSplit,
+                       std::conditional_t<OP == kOpDecode && W == 8 && (M == 5 || M == 6), SymbolDecodeSplit, NoSplit>>;
+
+template <int W, int M, int OP>
+struct PolyBody : PolyBodySplit<W, M, OP> {
   static constexpr int kW = W;
   static constexpr int kGroups = 1;
   static constexpr int kLayout = kLayoutSymbol;
@@ -425,13 +433,24 @@ struct MatRuntimeBody : NoSplit {
 };
 
 template <int W, int K, int M, int KIND, int OP>
-struct MatFixedBody : std::conditional_t<W == 16 && OP == kOpMatDecode, Wide16DecodeSplit, NoSplit> {
+using MatFixedBodySplit = std::conditional_t<
+    OP == kOpMatDecode && W == 16, Wide16DecodeSplit,
+    std::conditional_t<OP == kOpMatDecode && W == 8 && (M == 5 || M == 6),
+                       std::conditional_t<kind_layout(KIND) == kLayoutPacket, PacketDecodeSplit, SymbolDecodeSplit>,
+                       NoSplit>>;
+
+template <int W, int K, int M, int KIND, int OP>
+struct MatFixedBody : MatFixedBodySplit<W, K, M, KIND, OP> {
   static constexpr int kW = W;
   static constexpr int kGroups = 1;
   static constexpr int kLayout = kind_layout(KIND);
   static constexpr int kMaxOut = M;
+  // GF(2^16) packet-layout encodes (pure XOR networks, about 125
+  // registers) may run 15 consumer warps at the 128-register cap
   static constexpr int kMaxWarps =
-      MatFixedBody::kProducerWarps == 4 ? kSplitMaxConsumers : (OP == kOpMatEncode ? body_warps(M * W) : 8);
+      MatFixedBody::kProducerWarps == 4
+          ? kSplitMaxConsumers
+          : (OP == kOpMatEncode ? (W == 16 && kind_layout(KIND) == kLayoutPacket ? 15 : body_warps(M * W)) : 8);
   static constexpr int kMinBlocks =
       MatFixedBody::kProducerWarps == 4 ? 1 : body_min_blocks(W, kMaxWarps, (OP == kOpMatEncode ? 1 : 2) * M * W);
   __device__ static bool matches(const TileOp& o) { return o.op == OP && o.m == M && o.k == K; }

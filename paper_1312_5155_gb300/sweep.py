@@ -299,15 +299,20 @@ def mixed_batch_ops(seed, shapes, views, code):
     return ops
 
 
-def kmsweep():
+def kmsweep(points=None):
+    """§5.2 Fig. 3 and 4 on the GPU.  Every matrix realization runs a
+    compiled generator at every point when the library was built with
+    RSGB_BUILD_KM_CODES=1 (`compiled_generator` in each line says which)."""
+    from . import build
+    compiled = set(build.fixed_codes())
     seed = inputs.workload_seed("block_sizes")
     B = 1 << 20
-    for (k, m) in [(k, 4) for k in range(2, 21)] + [(10, m) for m in (2, 3, 5, 6)]:
+    for (k, m) in points or [(k, 4) for k in range(2, 21)] + [(10, m) for m in (2, 3, 5, 6)]:
         stripes = max(1, GIB // (k * B))
         for real in ("poly", "vandermonde", "cauchy", "good_cauchy"):
             r = _batch_pair(real, 8, k, m, B, stripes, seed, m, tag="km-")
             print(json.dumps({"sweep": "km", "k": k, "m": m, "B": B, "stripes": stripes, "realization": real,
-                              **r}), flush=True)
+                              "compiled_generator": real == "poly" or (8, k, m) in compiled, **r}), flush=True)
 
 
 def polyforms():
@@ -330,10 +335,13 @@ def main():
     ap.add_argument("name", nargs="+", choices=["single_stripe", "block_sizes", "gf16_blocks", "mixed_batch", "kmsweep",
                                                      "polyforms"])
     ap.add_argument("--blocks", default=None, help="block_sizes: comma-separated exponents i (B = 4 KiB * 2^i)")
+    ap.add_argument("--codes", default=None, help="kmsweep: comma-separated k:m points (default: the whole study)")
     a = ap.parse_args()
     for name in a.name:
         if name == "block_sizes" and a.blocks:
             block_sizes(blocks=[int(x) for x in a.blocks.split(",")])
+        elif name == "kmsweep" and a.codes:
+            kmsweep(points=[tuple(int(v) for v in x.split(":")) for x in a.codes.split(",")])
         else:
             globals()[name]()
 
