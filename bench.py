@@ -364,7 +364,11 @@ def run_e2e(args, wl, device):
         of every stripe, received into one staging buffer) go host->device,
         are decoded and the rebuilt blocks come back (staging_layout).
     Copies are transfers between pinned host memory and the device, inside
-    the timed region.  Each request stream has its own device and host
+    the timed region: host -> device as copy-engine transfers, device ->
+    host by the library's gather kernel (rs_copy_blocks), because on GB300
+    a copy-engine transfer in each direction at once measured 128 GB/s in
+    total, a copy engine one way and the kernel the other 296 GB/s (one
+    direction alone: 211 GB/s host -> device, 193 GB/s device -> host).  Each request stream has its own device and host
     buffers (the decode reads the parity stored by the warm-up's encode) and
     works in E2E_CHUNKS chunks of stripes: chunk c's input copy and launch go
     on one CUDA stream, its output copy on a second one, so the host->device
@@ -435,7 +439,12 @@ def run_e2e(args, wl, device):
                     coded.record(f["sin"])
                 f["sout"].wait_event(coded)
                 with torch.cuda.stream(f["sout"]):
-                    f["ho"][a:b].copy_(f["do"][a:b], non_blocking=True)
+                    # device -> host by the gather kernel, host -> device on
+                    # the copy engines: with both directions busy, one engine
+                    # transfer each way shared the link worst (see the docstring)
+                    src, dst = f["do"][a:b], f["ho"][a:b]
+                    rs.rs_copy_blocks([dst.data_ptr()], [src.data_ptr()], [src.numel()], stream=f["sout"],
+                                      engine_min_bytes=rs.ENGINE_NEVER)
                     ch["done"] = torch.cuda.Event()
                     ch["done"].record(f["sout"])
                 h2d += f["di"][a:b].numel()
