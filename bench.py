@@ -55,16 +55,20 @@ WORKLOAD = ("RS(10,4) GF(2^8), 1 GiB data in 102 stripes of 10 x 1 MiB blocks; p
 
 # DRAM traffic (dram__bytes_read.sum + dram__bytes_write.sum) per stripe of
 # each bench kernel, from one ncu capture of `python bench.py --profile-case
-# <op>` (16 stripes, one launch) divided by 16; a bench launch streams 102
-# stripes, so its traffic is 102 x this.  Valid only for the kernel sources
-# with the recorded digest (kernel_digest()); otherwise reported as null.
-TRAFFIC = {"digest": "6f2ce3ea6e45365f", "per_stripe": {
-    "poly_encode": 12743088,
-    "poly_decode": 12663488,
-    "vandermonde_encode": 12698432,
-    "vandermonde_decode": 12604864,
-    "cauchy_encode": 12635360,
-    "cauchy_decode": 13390512}}
+# <op> --profile-stripes 300` (one launch over 300 stripes, whose output is
+# nine times the L2, so the writes are counted too) divided by 300; a bench
+# launch streams 102 stripes, so its traffic is 102 x this.  Valid only for
+# the kernel sources with the recorded digest (kernel_digest()); otherwise
+# reported as null.
+TRAFFIC = {"digest": "be56377fa0c1726c", "per_stripe": {
+    "poly_encode": 14588817,
+    "poly_decode": 14579310,
+    "vandermonde_encode": 14575075,
+    "vandermonde_decode": 14572219,
+    "cauchy_encode": 14572962,
+    "cauchy_decode": 14898240,
+    "good_cauchy_encode": 14574784,
+    "good_cauchy_decode": 14946367}}
 
 
 def kernel_digest() -> str:
