@@ -210,7 +210,12 @@ rs_status rs_batch_set_launch(rs_batch *batch, int consumer_warps, int depth, in
 rs_status rs_batch_set(rs_batch *batch, const rs_op *ops, int n_ops, void *stream);
 
 /* Enqueue the batch's kernels on `stream` (one persistent launch per
- * kernel group; no host synchronisation, no allocation). */
+ * kernel group; no host synchronisation, no allocation).  The groups after
+ * the first run on the batch's own side streams, forked from `stream` and
+ * joined back into it: work queued on `stream` after this call waits for
+ * every group, and the groups' kernels may overlap one another, as the ops
+ * of one group already do -- so no op of a batch may read or write blocks
+ * another op of the same batch writes. */
 rs_status rs_batch_launch(rs_batch *batch, void *stream);
 
 /* Number of kernel launches rs_batch_launch enqueues for the current set. */
@@ -278,7 +283,7 @@ rs_status rs_copy_blocks(void *const *dst, const void *const *src, const size_t 
  * Set-up: the first call on a device looks up the array's device address
  * (cudaGetSymbolAddress, with that device current), and the first call for
  * each (w, m) on a device sets its encode kernel's shared-memory size
- * attribute; make those first calls before any stream capture.  The array
+ * attribute; later calls skip both steps.  The array
  * is shared by all calls on a device and keeps the last call's contents:
  * each call clears the status word and rewrites the tables before its
  * kernel runs, so calls whose work overlaps on the GPU race -- order them

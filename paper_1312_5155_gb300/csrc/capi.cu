@@ -400,6 +400,12 @@ struct rs_batch {
   size_t stage_bytes = 0;
   cudaEvent_t uploaded = nullptr;
   bool upload_pending = false;
+  // kernel groups after the first run on side streams forked from and
+  // joined back into the launch stream, so that a group's kernel fills the
+  // SMs that another group's tail leaves idle
+  cudaStream_t side[kMaxGroups - 1] = {};
+  cudaEvent_t fork = nullptr;
+  cudaEvent_t join[kMaxGroups - 1] = {};
   struct Group {
     const KernelEntry* entry;
     int layout;
@@ -425,6 +431,11 @@ size_t stage_layout(int max_ops, size_t* off_ptrs, size_t* off_coef, size_t* off
 }
 
 void batch_free(rs_batch* b) {
+  for (int i = 0; i < kMaxGroups - 1; ++i) {
+    if (b->side[i]) cudaStreamDestroy(b->side[i]);
+    if (b->join[i]) cudaEventDestroy(b->join[i]);
+  }
+  if (b->fork) cudaEventDestroy(b->fork);
   if (b->d_stripes) cudaFree(b->d_stripes);
   if (b->d_ptrs) cudaFree(b->d_ptrs);
   if (b->d_coef) cudaFree(b->d_coef);
@@ -635,6 +646,11 @@ rs_status rs_batch_create(int max_ops, rs_batch** out) {
   if (e == cudaSuccess) e = cudaMemset(b->d_status, 0, sizeof(int));
   if (e == cudaSuccess) e = cudaMallocHost(&b->h_stage, b->stage_bytes);
   if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->uploaded, cudaEventDisableTiming);
+  if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->fork, cudaEventDisableTiming);
+  for (int i = 0; i < kMaxGroups - 1 && e == cudaSuccess; ++i) {
+    e = cudaStreamCreateWithFlags(&b->side[i], cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->join[i], cudaEventDisableTiming);
+  }
   if (e != cudaSuccess) {
     batch_free(b);
     delete b;
@@ -783,7 +799,17 @@ rs_status rs_batch_launch(rs_batch* b, void* stream) {
   if (s != RS_OK) return s;
   JobParams* p = new (std::nothrow) JobParams();
   if (!p) return fail(RS_ENOMEM, "host allocation failed");
-  for (size_t g = 0; g < b->groups.size(); ++g) {
+  cudaStream_t st = (cudaStream_t)stream;
+  const size_t ng = b->groups.size();
+  if (ng > 1) {
+    cudaError_t e = cudaEventRecord(b->fork, st);
+    for (size_t g = 1; g < ng && e == cudaSuccess; ++g) e = cudaStreamWaitEvent(b->side[g - 1], b->fork, 0);
+    if (e != cudaSuccess) {
+      delete p;
+      return cuda_fail(e, "rs_batch_launch fork");
+    }
+  }
+  for (size_t g = 0; g < ng; ++g) {
     const rs_batch::Group& gr = b->groups[g];
     p->stripes = b->d_stripes + g * (size_t)b->max_ops;
     p->ptrs = b->d_ptrs;
@@ -796,7 +822,10 @@ rs_status rs_batch_launch(rs_batch* b, void* stream) {
     p->slot_bytes = gr.slot;
     p->packet_whole = gr.whole;
     p->depth = gr.depth;
-    cudaError_t e = gr.entry->launch(*p, gr.sh, (cudaStream_t)stream);
+    cudaStream_t gs = g == 0 ? st : b->side[g - 1];
+    cudaError_t e = gr.entry->launch(*p, gr.sh, gs);
+    if (e == cudaSuccess && g > 0) e = cudaEventRecord(b->join[g - 1], gs);
+    if (e == cudaSuccess && g > 0) e = cudaStreamWaitEvent(st, b->join[g - 1], 0);
     if (e != cudaSuccess) {
       delete p;
       return cuda_fail(e, gr.entry->name);

@@ -24,6 +24,7 @@ Names:
   polyforms the polynomial code as LFSR, through its generator matrix and
             through that matrix's bit-matrix (packets), RS(10,4), RS(12,4),
             RS(6,3), 1 MiB blocks
+  profile_gf16  one small GF(2^16) case (--op) for ncu
 
 Every line printed is one JSON object.  Bytes are algorithmic: encode
 (k + m) B, decode (k + e) B per stripe (min-read); "user_gbs" is k B / t.
@@ -207,6 +208,42 @@ def _percentile(xs, q):
     return xs[min(len(xs) - 1, max(0, int(math.ceil(q * len(xs))) - 1))]
 
 
+def profile_gf16(op="good_cauchy_encode", stripes=16, launches=3):
+    """A small GF(2^16) RS(12,4) 4 MiB-block case for ncu: `stripes`
+    stripes (16 = 1 GiB, larger than L2), one realization and op
+    ("<realization>_encode" or "<realization>_decode", 4 erasures), the
+    autotuned launch shape, an encode that makes the parity valid, then
+    `launches` launches of the op."""
+    torch = _torch()
+    real, kind = op.rsplit("_", 1)
+    k, m, w, B = 12, 4, 16, 4 << 20
+    seed = inputs.workload_seed("gf16_blocks")
+    n = k + m
+    buf = torch.empty((stripes, n, B), dtype=torch.uint8, device="cuda")
+    _fill(buf, seed, k, B, stripes)
+    code = rs.Code(k, m, w, real, packet_bytes=_packet(real, w, B))
+    rows = [list(buf[s]) for s in range(stripes)]
+    sms = torch.cuda.get_device_properties(0).multi_processor_count
+    enc_ops = [(code, "encode", [], rows[s], B) for s in range(stripes)]
+    enc = rs.Batch(stripes)
+    enc.set(enc_ops)
+    enc.launch()
+    if kind == "encode":
+        b, ops = enc, enc_ops
+    else:
+        b = rs.Batch(stripes)
+        ops = [(code, "decode", inputs.erasure_pattern(seed, s, n, m), rows[s], B) for s in range(stripes)]
+        b.set(ops)
+    shape, _ = autotune.tune_batch(b, ops, key=autotune.make_key(f"gf16-{stripes}-{kind}", real, k, m, w, B, sms))
+    torch.cuda.synchronize()
+    for _ in range(launches):
+        b.launch()
+    torch.cuda.synchronize()
+    if b.poll_status() != 0:
+        raise SystemExit("device status word set")
+    print(json.dumps({"profile_gf16": op, "stripes": stripes, "shape": list(shape)}), flush=True)
+
+
 def mixed_batch(stripes=4096, reps=5):
     """Config-4 batch: all stripes submitted at once.  Batched form = the
     persistent launches of one rs_batch, captured once in a CUDA graph and
@@ -333,13 +370,16 @@ def polyforms():
 def main():
     ap = argparse.ArgumentParser(description=__doc__, formatter_class=argparse.RawDescriptionHelpFormatter)
     ap.add_argument("name", nargs="+", choices=["single_stripe", "block_sizes", "gf16_blocks", "mixed_batch", "kmsweep",
-                                                     "polyforms"])
+                                                     "polyforms", "profile_gf16"])
+    ap.add_argument("--op", default="good_cauchy_encode", help="profile_gf16: <realization>_encode|_decode")
     ap.add_argument("--blocks", default=None, help="block_sizes: comma-separated exponents i (B = 4 KiB * 2^i)")
     ap.add_argument("--codes", default=None, help="kmsweep: comma-separated k:m points (default: the whole study)")
     a = ap.parse_args()
     for name in a.name:
         if name == "block_sizes" and a.blocks:
             block_sizes(blocks=[int(x) for x in a.blocks.split(",")])
+        elif name == "profile_gf16":
+            profile_gf16(a.op)
         elif name == "kmsweep" and a.codes:
             kmsweep(points=[tuple(int(v) for v in x.split(":")) for x in a.codes.split(",")])
         else:
