@@ -18,8 +18,10 @@ rank runs the same per-GPU workload on its own stripes (weak scaling, no
 collective on the data path); value = bytes of all ranks / max rank time.
 The line also carries `e2e` (the step through the C ABI with its host
 transfers), `serve` (request latency p50 / p99 of the continuous-batching
-server at half its saturation rate) and `cpu_baseline` (the CPU oracle on
-a bounded sample of the workload).
+server at half its saturation rate), `configs` (the GF(2^16) RS(12,4)
+configuration and the 4096-stripe mixed batch, measured after the step; see
+run_configs) and `cpu_baseline` (the CPU oracle on a bounded sample of the
+workload).
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 """
@@ -518,6 +520,37 @@ def _serial_capacity(pool, codes, seconds: float = 1.0) -> float:
     return sum(1 for r in reqs if r.done >= 0) / dt
 
 
+def run_configs():
+    """The other configurations of the metric, measured in the same run so
+    that they come with the bench line: RS(12,4) over GF(2^16) with 4 MiB
+    blocks (poly, Cauchy, good Cauchy; batched encode and decode with 1..4
+    erasures, 42 stripes) and the 4096-stripe mixed batch (codes (6,3)
+    (10,4) (12,4) (20,4), blocks of 4 KiB - 8 MiB, 30 % decodes; batched,
+    replayed from a CUDA graph, and as a loop of per-stripe calls, with
+    per-op completion latency).  GB/s of algorithmic bytes; frac = of the
+    HBM peak."""
+    import torch
+
+    from paper_1312_5155_gb300 import sweep
+    peak, kind = peaks()
+    out = {"hbm_peak_gbs": peak, "peak_kind": kind}
+    gf16 = {}
+    for r in sweep.gf16_blocks(emit=False):
+        row = {}
+        for key, v in r.items():
+            if isinstance(v, dict) and "gbs" in v:
+                row[key] = {"gbs": v["gbs"], "frac": round(v["gbs"] / peak, 3)}
+        gf16[r["realization"]] = row
+    out["gf16_rs12_4_4MiB_42stripes"] = gf16
+    torch.cuda.empty_cache()
+    mb = sweep.mixed_batch(emit=False)
+    torch.cuda.empty_cache()
+    mb["frac_batched"] = round(mb["batched"]["gbs"] / peak, 3)
+    mb["frac_graph_replay"] = round(mb["graph_replay"]["gbs"] / peak, 3)
+    out["mixed_batch_4096"] = mb
+    return out
+
+
 def run_serve():
     """The metric's serving part on this GPU (configuration 5's request mix):
     the continuous-batching server (paper_1312_5155_gb300.serve) under Poisson
@@ -747,6 +780,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-serve", action="store_true", help="skip the serving-latency measurement")
+    ap.add_argument("--no-configs", action="store_true",
+                    help="skip the GF(2^16) and 4096-stripe mixed-batch configurations")
     ap.add_argument("--no-tune", action="store_true", help="skip the launch-shape autotuner")
     ap.add_argument("--profile-case", default=None,
                     help="run one small kernel case for ncu, e.g. poly_encode, cauchy_decode")
@@ -783,6 +818,10 @@ def main():
         result["e2e"] = e2e
     if rank == 0 and not args.no_serve:
         result["serve"] = run_serve()
+    if rank == 0 and world == 1 and not args.no_configs:
+        del wl
+        torch.cuda.empty_cache()
+        result["configs"] = run_configs()
     if rank == 0:
         if world == 1 and not args.no_cpu_baseline:
             result["cpu_baseline"] = oracle_sample()

@@ -24,7 +24,8 @@ Names:
   polyforms the polynomial code as LFSR, through its generator matrix and
             through that matrix's bit-matrix (packets), RS(10,4), RS(12,4),
             RS(6,3), 1 MiB blocks
-  profile_gf16  one small GF(2^16) case (--op) for ncu
+  profile   one small case for ncu (--op, --code k:m, --w, --block, --stripes;
+            default RS(12,4) GF(2^16) 4 MiB x 16 stripes)
 
 Every line printed is one JSON object.  Bytes are algorithmic: encode
 (k + m) B, decode (k + e) B per stripe (min-read); "user_gbs" is k B / t.
@@ -154,11 +155,15 @@ def block_sizes(blocks=None, codes=((6, 3), (10, 4)), reals=("poly", "vandermond
                                   "packet_bytes": _packet(real, 8, B), **r}), flush=True)
 
 
-def gf16_blocks():
+def gf16_blocks(erasures=(1, 2, 3, 4), emit=True):
+    """Config 3: RS(12,4) over GF(2^16), 4 MiB blocks, 42 stripes (2.8 GB),
+    batched encode and decode with each erasure count, per realization.
+    Returns the result dicts (and prints each as a JSON line if `emit`)."""
     torch = _torch()
     k, m, w, B, stripes = 12, 4, 16, 4 << 20, 42
     seed = inputs.workload_seed("gf16_blocks")
     n = k + m
+    results = []
     for real in ("poly", "cauchy", "good_cauchy"):
         buf = torch.empty((stripes, n, B), dtype=torch.uint8, device="cuda")
         _fill(buf, seed, k, B, stripes)
@@ -171,7 +176,7 @@ def gf16_blocks():
         shape, _ = autotune.tune_batch(b, ops, key=autotune.make_key(f"gf16-{stripes}-encode", real, k, m, w, B, sms))
         ms = _time(b.launch)
         res["encode"] = {"ms": round(ms, 4), "gbs": round(stripes * n * B / ms / 1e6, 1), "shape": list(shape)}
-        for e in range(1, m + 1):
+        for e in erasures:
             d = rs.Batch(stripes)
             ops = [(code, "decode", inputs.erasure_pattern(seed, s, n, e), rows[s], B) for s in range(stripes)]
             autotune.tune_batch(d, ops, key=autotune.make_key(f"gf16-{stripes}-decode{e}", real, k, m, w, B, sms))
@@ -181,9 +186,12 @@ def gf16_blocks():
             res[f"decode_e{e}"] = {"ms": round(ms, 4), "gbs": round(stripes * (k + e) * B / ms / 1e6, 1)}
             d.close()
         b.close()
-        print(json.dumps({"workload": "gf16_blocks", "realization": real, "w": w, "B": B, "stripes": stripes, **res}), flush=True)
+        results.append({"workload": "gf16_blocks", "realization": real, "w": w, "B": B, "stripes": stripes, **res})
+        if emit:
+            print(json.dumps(results[-1]), flush=True)
         del buf
         torch.cuda.empty_cache()
+    return results
 
 
 def _graph_of(launch):
@@ -208,16 +216,17 @@ def _percentile(xs, q):
     return xs[min(len(xs) - 1, max(0, int(math.ceil(q * len(xs))) - 1))]
 
 
-def profile_gf16(op="good_cauchy_encode", stripes=16, launches=3):
-    """A small GF(2^16) RS(12,4) 4 MiB-block case for ncu: `stripes`
-    stripes (16 = 1 GiB, larger than L2), one realization and op
-    ("<realization>_encode" or "<realization>_decode", 4 erasures), the
-    autotuned launch shape, an encode that makes the parity valid, then
-    `launches` launches of the op."""
+def profile(op="good_cauchy_encode", k=12, m=4, w=16, B=4 << 20, stripes=16, launches=3):
+    """One small case for ncu: `stripes` stripes of RS(k, m) over GF(2^w)
+    with B-byte blocks (the default, 16 stripes of RS(12,4) GF(2^16) 4 MiB,
+    is 1 GiB, larger than L2), one realization and op ("<realization>_encode"
+    or "<realization>_decode", m erasures), the autotuned launch shape (tuned
+    in the run before ncu's, then read from the tuner's cache), an encode
+    that makes the parity valid, then `launches` launches of the op."""
     torch = _torch()
     real, kind = op.rsplit("_", 1)
-    k, m, w, B = 12, 4, 16, 4 << 20
-    seed = inputs.workload_seed("gf16_blocks")
+    tag = "gf16" if (k, m, w, B) == (12, 4, 16, 4 << 20) else f"prof{k}-{m}-{w}-{B}"
+    seed = inputs.workload_seed("gf16_blocks" if w == 16 else "block_sizes")
     n = k + m
     buf = torch.empty((stripes, n, B), dtype=torch.uint8, device="cuda")
     _fill(buf, seed, k, B, stripes)
@@ -234,17 +243,19 @@ def profile_gf16(op="good_cauchy_encode", stripes=16, launches=3):
         b = rs.Batch(stripes)
         ops = [(code, "decode", inputs.erasure_pattern(seed, s, n, m), rows[s], B) for s in range(stripes)]
         b.set(ops)
-    shape, _ = autotune.tune_batch(b, ops, key=autotune.make_key(f"gf16-{stripes}-{kind}", real, k, m, w, B, sms))
+    shape, _ = autotune.tune_batch(b, ops, key=autotune.make_key(f"{tag}-{stripes}-{kind}", real, k, m, w, B, sms),
+                                   candidates=autotune.CANDIDATES)
     torch.cuda.synchronize()
     for _ in range(launches):
         b.launch()
     torch.cuda.synchronize()
     if b.poll_status() != 0:
         raise SystemExit("device status word set")
-    print(json.dumps({"profile_gf16": op, "stripes": stripes, "shape": list(shape)}), flush=True)
+    print(json.dumps({"profile": op, "k": k, "m": m, "w": w, "B": B, "stripes": stripes, "shape": list(shape)}),
+          flush=True)
 
 
-def mixed_batch(stripes=4096, reps=5):
+def mixed_batch(stripes=4096, reps=5, emit=True):
     """Config-4 batch: all stripes submitted at once.  Batched form = the
     persistent launches of one rs_batch, captured once in a CUDA graph and
     replayed; per-stripe form = one rs_encode / rs_decode call per stripe on
@@ -309,7 +320,7 @@ def mixed_batch(stripes=4096, reps=5):
         e1.record()
         torch.cuda.synchronize()
         lat_graph.append(e0.elapsed_time(e1))
-    print(json.dumps({"workload": "mixed_batch", "stripes": stripes, "bytes": nbytes,
+    res = {"workload": "mixed_batch", "stripes": stripes, "bytes": nbytes,
                       "gib_resident": round(total / GIB, 2), "decodes": sum(1 for x in shapes if x[3]),
                       "kernel_launches_batched": b.kernel_count, "launch_shape": list(shape),
                       "batched": {"ms": round(ms_batch, 3), "gbs": round(nbytes / ms_batch / 1e6, 1)},
@@ -318,10 +329,12 @@ def mixed_batch(stripes=4096, reps=5):
                                        "op_latency_p99_ms": round(max(lat_graph), 3)},
                       "per_stripe_loop": {"ms": round(ms_loop, 3), "gbs": round(nbytes / ms_loop / 1e6, 1),
                                           "op_latency_p50_ms": round(_percentile(lat_loop, 0.5), 3),
-                                          "op_latency_p99_ms": round(_percentile(lat_loop, 0.99), 3)}}),
-          flush=True)
+                                          "op_latency_p99_ms": round(_percentile(lat_loop, 0.99), 3)}}
+    if emit:
+        print(json.dumps(res), flush=True)
     b.close()
     enc_all.close()
+    return res
 
 
 def mixed_batch_ops(seed, shapes, views, code):
@@ -370,16 +383,21 @@ def polyforms():
 def main():
     ap = argparse.ArgumentParser(description=__doc__, formatter_class=argparse.RawDescriptionHelpFormatter)
     ap.add_argument("name", nargs="+", choices=["single_stripe", "block_sizes", "gf16_blocks", "mixed_batch", "kmsweep",
-                                                     "polyforms", "profile_gf16"])
-    ap.add_argument("--op", default="good_cauchy_encode", help="profile_gf16: <realization>_encode|_decode")
+                                                     "polyforms", "profile"])
+    ap.add_argument("--op", default="good_cauchy_encode", help="profile: <realization>_encode|_decode")
+    ap.add_argument("--code", default="12:4", help="profile: k:m")
+    ap.add_argument("--w", type=int, default=16, help="profile: field width")
+    ap.add_argument("--block", type=int, default=4 << 20, help="profile: block bytes")
+    ap.add_argument("--stripes", type=int, default=16, help="profile: stripes")
     ap.add_argument("--blocks", default=None, help="block_sizes: comma-separated exponents i (B = 4 KiB * 2^i)")
     ap.add_argument("--codes", default=None, help="kmsweep: comma-separated k:m points (default: the whole study)")
     a = ap.parse_args()
     for name in a.name:
         if name == "block_sizes" and a.blocks:
             block_sizes(blocks=[int(x) for x in a.blocks.split(",")])
-        elif name == "profile_gf16":
-            profile_gf16(a.op)
+        elif name == "profile":
+            pk, pm = (int(x) for x in a.code.split(":"))
+            profile(a.op, pk, pm, a.w, a.block, a.stripes)
         elif name == "kmsweep" and a.codes:
             kmsweep(points=[tuple(int(v) for v in x.split(":")) for x in a.codes.split(",")])
         else:
