@@ -21,7 +21,7 @@ import os
 import threading
 
 CANDIDATES = [(16, 8, 1), (16, 12, 1), (15, 5, 1), (15, 4, 1), (15, 3, 1), (12, 6, 1), (12, 4, 1), (12, 3, 1),
-              (8, 16, 1), (8, 8, 2), (8, 12, 2), (4, 16, 2), (4, 8, 3), (2, 8, 4)]
+              (8, 16, 1), (8, 8, 2), (8, 12, 2), (4, 16, 2), (4, 8, 3), (4, 8, 4), (2, 8, 4)]
 _DEFAULT_CACHE = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "_build",
                               "autotune.json")
 _lock = threading.Lock()

@@ -146,8 +146,9 @@ struct MatEncodeFixed {
   }
 };
 
-// Compile-time-P encode on two 32-column groups per thread (symbol layout).
-template <int W, int K, int M, int KIND>
+// Compile-time-P encode on two 32-column groups per thread (symbol layout,
+// with transposes; packet layout without: group g is word g of the unit).
+template <int W, int K, int M, int KIND, bool kTranspose = true>
 struct MatEncodeFixed2 {
   template <class Src, class Dst>
   static RS_HD void run(Src& src, Dst& dst) {
@@ -159,8 +160,10 @@ struct MatEncodeFixed2 {
     StaticFor<0, K>::run([&](auto J) {
       uint32_t x[2 * W];
       src.load(decltype(J)::value, x);
-      transpose<W>(x);
-      transpose<W>(x + W);
+      if (kTranspose) {
+        transpose<W>(x);
+        transpose<W>(x + W);
+      }
       StaticFor<0, M>::run([&](auto I) {
         constexpr uint32_t c = ParityMatrix<W, K, M, KIND>::value.a[decltype(I)::value][decltype(J)::value];
         mul_acc<W, c>(a[decltype(I)::value], x);
@@ -175,8 +178,10 @@ struct MatEncodeFixed2 {
         y[c] = a[i][c];
         y[W + c] = b[i][c];
       }
-      transpose<W>(y);
-      transpose<W>(y + W);
+      if (kTranspose) {
+        transpose<W>(y);
+        transpose<W>(y + W);
+      }
       dst.store(i, y);
     }
   }

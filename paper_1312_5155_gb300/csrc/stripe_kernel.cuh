@@ -307,23 +307,30 @@ struct ColumnWords {
 // ------------------------------------------------------------------ bodies
 // Register split: the producer gets a warpgroup of its own (4 warps, one of
 // them working) that gives back registers with setmaxnreg.dec, and the
-// consumer warpgroups take them with setmaxnreg.inc.  A CTA of 4 + 12 warps
-// is launched at 128 registers a thread (the 64K of an SM); the producer
-// warpgroup drops to P, the 12 consumer warps rise to C, with
-// 128 P + 384 C <= 65536, so every launch of 4, 8 or 12 consumer warps fits
-// (the shares are checked against the compiled count before the first
-// launch).  Used where the extra registers were measured to pay: the
-// two-group decodes with pair sums in the decode-matrix step, and the
-// GF(2^16) decodes (12 instead of 8 consumer warps).  The packet-layout
-// producer needs more registers than the symbol-layout one.
+// consumer warpgroups take them with setmaxnreg.inc.  A CTA of 4 + NC warps
+// is launched at the registers a thread its size allows (128 for 4 + 12
+// warps: the 64K of an SM; 168 for 4 + 8); the producer warpgroup drops to
+// P, the NC consumer warps rise to C, with 128 P + 32 NC C at most the
+// launch's registers, so every launch of fewer consumer warps fits too (the
+// shares are checked against the compiled count before the first launch).
+// Used where the extra registers were measured to pay: the two-group
+// decodes with pair sums in the decode-matrix step, the GF(2^16) decodes
+// (12 instead of 8 consumer warps) and the GF(2^16) two-group packet
+// encode.  The packet-layout producer needs more registers than the
+// symbol-layout one.
 constexpr int kSplitMaxConsumers = 12;
-template <int P, int C>
+// registers a thread at launch for a CTA of `threads` threads (warps take
+// registers in groups of four, a thread's count is a multiple of 8)
+RS_CHD constexpr int launch_regs(int threads) { return 65536 / ((threads + 127) / 128 * 128) / 8 * 8; }
+template <int P, int C, int NC = kSplitMaxConsumers>
 struct RegSplit {
-  static_assert(P % 8 == 0 && C % 8 == 0 && P * 128 + C * 32 * kSplitMaxConsumers <= 65536,
+  static_assert(NC % 4 == 0 && P % 8 == 0 && C % 8 == 0 && C <= 256 &&
+                    P * 128 + C * 32 * NC <= launch_regs((NC + 4) * 32) * (NC + 4) * 32,
                 "register split exceeds the launch's registers");
   static constexpr int kProducerWarps = 4;
   static constexpr int kProducerRegs = P;
   static constexpr int kConsumerRegs = C;
+  static constexpr int kSplitConsumers = NC;
 };
 struct NoSplit {
   static constexpr int kProducerWarps = 1;
@@ -333,6 +340,7 @@ struct NoSplit {
 using SymbolDecodeSplit = RegSplit<56, 152>;  // two-group symbol-layout decode, pair sums
 using PacketDecodeSplit = RegSplit<80, 144>;  // two-group packet-layout decode, pair sums
 using Wide16DecodeSplit = RegSplit<104, 136>; // GF(2^16) one-group decodes
+using Packet16Encode2Split = RegSplit<96, 200, 8>;  // GF(2^16) two-group packet encode
 
 RS_CHD constexpr int body_warps(int regs_words) { return regs_words <= 48 ? 16 : 8; }
 // Register budget: 8-warp GF(2^8) bodies whose live state (accumulators,
@@ -373,21 +381,27 @@ struct PolyBody : PolyBodySplit<W, M, OP> {
   }
 };
 
-// Compile-time-P encode with two 32-column groups per lane (symbol layout,
-// GF(2^8), M <= 4): MatEncodeFixed2.
+// Compile-time-P encode with two 32-column groups per lane: MatEncodeFixed2.
+// Symbol layout (GF(2^8), M <= 4): 12 warps at 128 registers.  Packet
+// layout over GF(2^16): the 2 x M x 16 accumulator planes need the register
+// split's 200 registers, 8 consumer warps; a tile of 8 x 32 units of two
+// words is then one whole super-packet of 2 KiB packets, fetched by one
+// bulk copy per block (the one-group kernel's 480-unit tiles straddle the
+// 512-unit super-packets).
 template <int W, int K, int M, int KIND>
-struct MatFixedEncode2Body : NoSplit {
+struct MatFixedEncode2Body
+    : std::conditional_t<kind_layout(KIND) == kLayoutPacket, Packet16Encode2Split, NoSplit> {
   static constexpr int kW = W;
   static constexpr int kGroups = 2;
-  static constexpr int kLayout = kLayoutSymbol;
+  static constexpr int kLayout = kind_layout(KIND);
   static constexpr int kMaxOut = M;
-  static constexpr int kMaxWarps = 12;
+  static constexpr int kMaxWarps = kLayout == kLayoutPacket ? Packet16Encode2Split::kSplitConsumers : 12;
   static constexpr int kMinBlocks = 1;
-  static_assert(kind_layout(KIND) == kLayoutSymbol, "symbol-layout kinds only");
+  static_assert(kLayout == kLayoutSymbol || W == 16, "packet layout: GF(2^16) only");
   __device__ static bool matches(const TileOp& o) { return o.op == kOpMatEncode && o.m == M && o.k == K; }
   template <class Tile>
   __device__ static void run(const TileOp&, Tile& t, const uint32_t*) {
-    MatEncodeFixed2<W, K, M, KIND>::run(t, t);
+    MatEncodeFixed2<W, K, M, KIND, kLayout == kLayoutSymbol>::run(t, t);
   }
 };
 

@@ -307,6 +307,22 @@ int mat_fixed2_packet(const DecodePlan* pl, uint8_t* blocks, size_t B, size_t P)
   return 0;
 }
 
+// The two-column-group compile-time-P encode in the packet layout (the
+// GF(2^16) kernel's body; no transposes).
+template <int W, int K, int M, int KIND>
+int mat_encode2_packet(uint8_t* blocks, size_t B, size_t P) {
+  std::vector<const uint8_t*> in;
+  std::vector<uint8_t*> out;
+  for (int j = 0; j < K; ++j) in.push_back(blocks + (size_t)j * B);
+  for (int i = 0; i < M; ++i) out.push_back(blocks + (size_t)(K + i) * B);
+  for (size_t sp = 0; sp < B; sp += (size_t)W * P)
+    for (size_t u = 0; u < P / 8; ++u) {
+      HostPacketTile2<W> t{in.data(), out.data(), sp, P, u};
+      MatEncodeFixed2<W, K, M, KIND, false>::run(t, t);
+    }
+  return 0;
+}
+
 template <int K, int M, int KIND>
 int mat_encode2(uint8_t* blocks, size_t B) {
   std::vector<const uint8_t*> in;
@@ -494,6 +510,14 @@ int emu_mat_decode2(int w, int k, int m, int kind, const int* er, int e, int rea
 
 // Two-column-group matrix decode in the packet layout (GF(2^8), kinds 2 and
 // 4; P = packet bytes, a multiple of 8 dividing B / 8).
+// The GF(2^16) two-group packet-layout encode (kinds 2 and 5, RS(12,4)).
+int emu_mat_encode2_packet(int w, int k, int m, int kind, uint8_t* blocks, size_t B, size_t P) {
+  if (w != 16 || k != 12 || m != 4 || P % 8 || B % (16 * P)) return -2;
+  if (kind == 2) return mat_encode2_packet<16, 12, 4, 2>(blocks, B, P);
+  if (kind == 5) return mat_encode2_packet<16, 12, 4, 5>(blocks, B, P);
+  return -2;
+}
+
 int emu_mat_decode2_packet(int w, int k, int m, int kind, const int* er, int e, int read_all, uint8_t* blocks,
                            size_t B, size_t P) {
   if (w != 8 || (kind != 2 && kind != 4 && kind != 5) || e <= 0 || P % 8 || B % (8 * P)) return -2;

@@ -187,3 +187,19 @@ def test_two_group_packet_decode_matches_oracle(emu, real, k, m, pkt, sp, read_a
                                         B, pkt)
         assert rc == 0, rc
         assert np.array_equal(got, base), er
+
+
+@pytest.mark.parametrize("real,pkt,sp", [("cauchy", 256, 2), ("good_cauchy", 2048, 1), ("good_cauchy", 128, 3)])
+def test_gf16_two_group_packet_encode_matches_oracle(emu, real, pkt, sp):
+    """The GF(2^16) packet-layout encode with two adjacent words per thread
+    (the kernel that covers a whole super-packet per tile)."""
+    emu.emu_mat_encode2_packet.argtypes = [ctypes.c_int] * 4 + [U8P, ctypes.c_size_t, ctypes.c_size_t]
+    w, k, m = 16, 12, 4
+    B = sp * w * pkt
+    ref = make_stripe(w, k, m, B)
+    O.encode(real, w, k, m, ref, packet_bytes=pkt)
+    got = ref.copy()
+    got[k:] = 0xA5
+    rc = emu.emu_mat_encode2_packet(w, k, m, KIND[real], got.ctypes.data_as(U8P), B, pkt)
+    assert rc == 0, rc
+    assert np.array_equal(got, ref)
