@@ -524,10 +524,12 @@ def run_configs():
     """The other configurations of the metric, measured in the same run so
     that they come with the bench line: RS(12,4) over GF(2^16) with 4 MiB
     blocks (poly, Cauchy, good Cauchy; batched encode and decode with 1..4
-    erasures, 42 stripes) and the 4096-stripe mixed batch (codes (6,3)
-    (10,4) (12,4) (20,4), blocks of 4 KiB - 8 MiB, 30 % decodes; batched,
-    replayed from a CUDA graph, and as a loop of per-stripe calls, with
-    per-op completion latency).  GB/s of algorithmic bytes; frac = of the
+    erasures, 42 stripes), five points of the block-size and k studies
+    (RS(10,4) at 4 KiB, 64 KiB and 16 MiB blocks, RS(6,3) and RS(20,4) at
+    1 MiB; poly, Vandermonde, good Cauchy) and the 4096-stripe mixed batch
+    (codes (6,3) (10,4) (12,4) (20,4), blocks of 4 KiB - 8 MiB, 30 %
+    decodes; batched, replayed from a CUDA graph, and as a loop of
+    per-stripe calls, with per-op completion latency).  GB/s of algorithmic bytes; frac = of the
     HBM peak."""
     import torch
 
@@ -543,6 +545,19 @@ def run_configs():
         gf16[r["realization"]] = row
     out["gf16_rs12_4_4MiB_42stripes"] = gf16
     torch.cuda.empty_cache()
+    # points of the block-size and k studies: 1 GiB of data each, m seeded
+    # erasures per decode, tuned launch shapes
+    seed = workload_seed("block_sizes")
+    pts = {}
+    for (k, m, B) in ((10, 4, 4 << 10), (10, 4, 64 << 10), (10, 4, 16 << 20), (6, 3, 1 << 20), (20, 4, 1 << 20)):
+        stripes = max(1, (1 << 30) // (k * B))
+        row = {}
+        for real in ("poly", "vandermonde", "good_cauchy"):
+            r = sweep._batch_pair(real, 8, k, m, B, stripes, seed, m, tag="bench-")
+            row[real] = {op: {"gbs": r[op]["gbs"], "frac": round(r[op]["gbs"] / peak, 3)} for op in ("encode", "decode")}
+        pts[f"rs{k}_{m}_B{B >> 10}KiB"] = row
+        torch.cuda.empty_cache()
+    out["block_and_k_points"] = pts
     mb = sweep.mixed_batch(emit=False)
     torch.cuda.empty_cache()
     mb["frac_batched"] = round(mb["batched"]["gbs"] / peak, 3)

@@ -93,10 +93,14 @@ def instances():
                     out.append((name + "_g2", f"MatFixedDecode2Body<{w}, {k}, {m}, {kind}>", dict(key, wide=1)))
                 elif layout == 0:
                     out.append((name + "_g2", f"MatFixedEncode2Body<{w}, {k}, {m}, {kind}>", dict(key, wide=1)))
-            # GF(2^16) packet-layout encodes: two groups on 8 consumer warps
-            # (whole super-packets per tile)
-            if w == 16 and layout == 1 and op == 2:
-                out.append((name + "_g2", f"MatFixedEncode2Body<{w}, {k}, {m}, {kind}>", dict(key, wide=1)))
+            # GF(2^16) packet layout: two groups on 8 consumer warps (whole
+            # super-packets per tile).  Encodes, and the good Cauchy decode
+            # (e = 4: 3624 -> 4108 GB/s); the plain Cauchy decode's larger
+            # XOR network misses the instruction cache with two groups
+            # (3272 -> 2951), so it keeps the one-group kernel.
+            if w == 16 and layout == 1 and (op == 2 or kind == 5):
+                body = "MatFixedEncode2Body" if op == 2 else "MatFixedDecode2Body"
+                out.append((name + "_g2", f"{body}<{w}, {k}, {m}, {kind}>", dict(key, wide=1)))
     for (w, ms) in MIXED_POLY:
         bodies = ", ".join(f"PolyBody<{w}, {m}, {op}>" for m in ms for op in (0, 1))
         mset = sum(1 << m for m in ms)

@@ -33,6 +33,13 @@ struct MatKM {
   uint32_t a[M][K];
 };
 
+// Entry (i, j) of a MatKM by reference (the accessor good_cauchy_scale takes).
+template <int K, int M>
+struct MatKMEntry {
+  MatKM<K, M>& p;
+  RS_CHD constexpr uint32_t& operator()(int i, int j) const { return p.a[i][j]; }
+};
+
 // Gauss-Jordan inverse over GF(2^w) of a K x K matrix, at compile time.
 template <int K>
 RS_CHD constexpr bool ct_invert(uint32_t (&A)[K][K], uint32_t (&R)[K][K], int w) {
@@ -88,7 +95,7 @@ struct ParityMatrix {
       for (int i = 0; i < M; ++i)
         for (int j = 0; j < K; ++j) P.a[i][j] = gf_inv((uint32_t)i ^ (uint32_t)(M + j), W);
       if (KIND == kKindGoodCauchy)
-        good_cauchy_scale([&P](int i, int j) -> uint32_t& { return P.a[i][j]; }, K, M, W);
+        good_cauchy_scale(MatKMEntry<K, M>{P}, K, M, W);
     } else {
       uint32_t top[K][K] = {};
       uint32_t inv[K][K] = {};

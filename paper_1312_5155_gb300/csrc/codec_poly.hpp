@@ -179,6 +179,9 @@ RS_HD void fold_and_select2(uint32_t sel, uint32_t* y0, uint32_t* y1, const uint
   if constexpr (W == 8) {
     fold_select2_w8<ROT, NS>(sel, y0, y1, A, B);
     return;
+  } else if constexpr (W == 16) {
+    fold_select2_w16<ROT, NS>(sel, y0, y1, A, B);
+    return;
   }
 #endif
   mul_alpha_renamed<W, ROT - 1>(y0);

@@ -340,7 +340,7 @@ struct NoSplit {
 using SymbolDecodeSplit = RegSplit<56, 152>;  // two-group symbol-layout decode, pair sums
 using PacketDecodeSplit = RegSplit<80, 144>;  // two-group packet-layout decode, pair sums
 using Wide16DecodeSplit = RegSplit<104, 136>; // GF(2^16) one-group decodes
-using Packet16Encode2Split = RegSplit<96, 200, 8>;  // GF(2^16) two-group packet encode
+using Packet16Encode2Split = RegSplit<96, 200, 8>;  // GF(2^16) two-group packet encode and decode
 
 RS_CHD constexpr int body_warps(int regs_words) { return regs_words <= 48 ? 16 : 8; }
 // Register budget: 8-warp GF(2^8) bodies whose live state (accumulators,
@@ -481,22 +481,29 @@ struct MatFixedBody : MatFixedBodySplit<W, K, M, KIND, OP> {
 
 // Compile-time-P decode (M <= 4) with two 32-column groups per lane
 // (MatDecodeFixed2), in either layout.
+template <int W, int KIND>
+using Decode2Split = std::conditional_t<kind_layout(KIND) == kLayoutPacket,
+                                        std::conditional_t<W == 16, Packet16Encode2Split, PacketDecodeSplit>, NoSplit>;
 template <int W, int K, int M, int KIND>
-struct MatFixedDecode2Body : std::conditional_t<kind_layout(KIND) == kLayoutPacket, PacketDecodeSplit, NoSplit> {
+struct MatFixedDecode2Body : Decode2Split<W, KIND> {
   static constexpr int kW = W;
   static constexpr int kGroups = 2;
   static constexpr int kLayout = kind_layout(KIND);
   static constexpr int kMaxOut = M;
   // symbol layout: up to 15 warps at 128 registers (the pair sums measured
-  // slower there: they spill at the split's budget); packet layout: the
-  // register split and pair sums, 12 warps at 144 registers
-  static constexpr int kMaxWarps = kLayout == kLayoutSymbol ? 15 : kSplitMaxConsumers;
+  // slower there: they spill at the split's budget); packet layout over
+  // GF(2^8): the register split and pair sums, 12 warps at 144 registers;
+  // over GF(2^16): 8 warps at 200 registers without pair sums (a tile of 256
+  // two-word units is one super-packet of 2 KiB packets, as in the encode)
+  static constexpr bool kPairSums = kLayout == kLayoutPacket && W == 8;
+  static constexpr int kMaxWarps =
+      kLayout == kLayoutSymbol ? 15 : (W == 16 ? Packet16Encode2Split::kSplitConsumers : kSplitMaxConsumers);
   static constexpr int kMinBlocks = 1;
   __device__ static bool matches(const TileOp& o) { return o.op == kOpMatDecode && o.m == M && o.k == K; }
   template <class Tile>
   __device__ static void run(const TileOp& o, Tile& t, const uint32_t* coef) {
     CoefWords cm{coef};
-    MatDecodeFixed2<W, K, M, KIND, kLayout == kLayoutSymbol, kLayout == kLayoutPacket>::run(o.read_mask, o.e, t, t, cm);
+    MatDecodeFixed2<W, K, M, KIND, kLayout == kLayoutSymbol, kPairSums>::run(o.read_mask, o.e, t, t, cm);
   }
 };
 

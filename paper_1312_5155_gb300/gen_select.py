@@ -153,6 +153,9 @@ def render() -> str:
         "// one 32-column group, GF(2^16), no pair sums",
         gen_function("fold_select_w16", 16, 1, False),
         "",
+        "// two 32-column groups, GF(2^16), no pair sums",
+        gen_function("fold_select2_w16", 16, 2, False),
+        "",
         "}  // namespace rsgb",
         "#endif",
         "",

@@ -291,7 +291,8 @@ struct HostPacketTile2 {
   }
 };
 
-// The two-column-group compile-time-P decode in the packet layout.
+// The two-column-group compile-time-P decode in the packet layout (pair
+// sums over GF(2^8), none over GF(2^16), as the kernels).
 template <int W, int K, int M, int KIND>
 int mat_fixed2_packet(const DecodePlan* pl, uint8_t* blocks, size_t B, size_t P) {
   std::vector<const uint8_t*> in;
@@ -302,7 +303,7 @@ int mat_fixed2_packet(const DecodePlan* pl, uint8_t* blocks, size_t B, size_t P)
   for (size_t sp = 0; sp < B; sp += (size_t)W * P)
     for (size_t u = 0; u < P / 8; ++u) {
       HostPacketTile2<W> t{in.data(), out.data(), sp, P, u};
-      MatDecodeFixed2<W, K, M, KIND, false, true>::run(pl->read_mask, pl->e, t, t, cf);  // pair sums, as the kernel
+      MatDecodeFixed2<W, K, M, KIND, false, W == 8>::run(pl->read_mask, pl->e, t, t, cf);
     }
   return 0;
 }
@@ -520,13 +521,20 @@ int emu_mat_encode2_packet(int w, int k, int m, int kind, uint8_t* blocks, size_
 
 int emu_mat_decode2_packet(int w, int k, int m, int kind, const int* er, int e, int read_all, uint8_t* blocks,
                            size_t B, size_t P) {
-  if (w != 8 || (kind != 2 && kind != 4 && kind != 5) || e <= 0 || P % 8 || B % (8 * P)) return -2;
+  if ((w != 8 && w != 16) || (kind != 2 && kind != 4 && kind != 5) || e <= 0 || P % 8 || B % ((size_t)w * P))
+    return -2;
   std::vector<uint32_t> Pm;
   if (!host_parity(w, k, m, kind, Pm)) return -3;
   DecodePlan pl;
   std::string err;
   if (!make_matrix_decode_plan(k, m, w, Pm, er, e, read_all != 0, pl, err)) return -1;
   if (pl.M > 4) return -2;
+  if (w == 16) {
+    if (k != 12 || m != 4) return -2;
+    if (kind == 2) return mat_fixed2_packet<16, 12, 4, 2>(&pl, blocks, B, P);
+    if (kind == 5) return mat_fixed2_packet<16, 12, 4, 5>(&pl, blocks, B, P);
+    return -2;
+  }
   if (kind == 2) {
     if (k == 10 && m == 4) return mat_fixed2_packet<8, 10, 4, 2>(&pl, blocks, B, P);
     if (k == 6 && m == 3) return mat_fixed2_packet<8, 6, 3, 2>(&pl, blocks, B, P);

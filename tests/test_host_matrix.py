@@ -203,3 +203,27 @@ def test_gf16_two_group_packet_encode_matches_oracle(emu, real, pkt, sp):
     rc = emu.emu_mat_encode2_packet(w, k, m, KIND[real], got.ctypes.data_as(U8P), B, pkt)
     assert rc == 0, rc
     assert np.array_equal(got, ref)
+
+
+@pytest.mark.parametrize("real,pkt,sp", [("cauchy", 256, 1), ("good_cauchy", 128, 2)])
+def test_gf16_two_group_packet_decode_matches_oracle(emu, real, pkt, sp):
+    """The GF(2^16) packet-layout decode with two adjacent words per thread
+    (no pair sums): every erasure count, min-read and read-all."""
+    emu.emu_mat_decode2_packet.argtypes = [ctypes.c_int] * 4 + [ctypes.POINTER(ctypes.c_int), ctypes.c_int,
+                                                                ctypes.c_int, U8P, ctypes.c_size_t, ctypes.c_size_t]
+    w, k, m = 16, 12, 4
+    n = k + m
+    B = sp * w * pkt
+    base = make_stripe(w, k, m, B)
+    O.encode(real, w, k, m, base, packet_bytes=pkt)
+    rng = np.random.default_rng(pkt + sp)
+    for e in range(1, m + 1):
+        for read_all in (False, True):
+            er = sorted(int(x) for x in rng.choice(n, e, replace=False))
+            got = base.copy()
+            got[er] = 0x3C
+            arr = (ctypes.c_int * e)(*er)
+            rc = emu.emu_mat_decode2_packet(w, k, m, KIND[real], arr, e, int(read_all), got.ctypes.data_as(U8P), B,
+                                            pkt)
+            assert rc == 0, rc
+            assert np.array_equal(got, base), (er, read_all)
