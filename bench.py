@@ -62,15 +62,15 @@ WORKLOAD = ("RS(10,4) GF(2^8), 1 GiB data in 102 stripes of 10 x 1 MiB blocks; p
 # launch streams 102 stripes, so its traffic is 102 x this.  Valid only for
 # the kernel sources with the recorded digest (kernel_digest()); otherwise
 # reported as null.
-TRAFFIC = {"digest": "be56377fa0c1726c", "per_stripe": {
-    "poly_encode": 14588817,
-    "poly_decode": 14579310,
-    "vandermonde_encode": 14575075,
-    "vandermonde_decode": 14572219,
-    "cauchy_encode": 14572962,
-    "cauchy_decode": 14898240,
-    "good_cauchy_encode": 14574784,
-    "good_cauchy_decode": 14946367}}
+TRAFFIC = {"digest": "779dd8810daccce9", "per_stripe": {
+    "poly_encode": 14587484,
+    "poly_decode": 14579054,
+    "vandermonde_encode": 14574441,
+    "vandermonde_decode": 14572961,
+    "cauchy_encode": 14575762,
+    "cauchy_decode": 14906356,
+    "good_cauchy_encode": 14575753,
+    "good_cauchy_decode": 14949050}}
 
 
 def kernel_digest() -> str:
@@ -717,7 +717,7 @@ def oracle_sample(seconds_target: float = 12.0, runs: int = 3):
             "single_thread_per_run_gbs": [round(v, 4) for v, _ in single],
             **info,
             "sample": f"whole stripes of the 102 RS(10,4) 1 MiB-block stripes, encode + 4-erasure decode in each "
-                      f"of the 3 realizations per stripe pass; all-core: {runs} runs of {cores} threads x "
+                      f"of the {len(REALIZATIONS)} realizations per stripe pass; all-core: {runs} runs of {cores} threads x "
                       f"{all_passes} passes (one stripe per thread at a time); single-thread: {runs} runs of "
                       f"{one_passes} passes; value = mean of the all-core runs"}
 
@@ -733,7 +733,7 @@ def run_reference(args, rank, world):
     samples = [oracle_run(cores, passes, first=1 + i * cores * passes)[0] for i in range(args.steps)]
     v = statistics.mean(samples)
     base = {"cores": cores, "sample": f"{args.steps} steps of {cores} threads x {passes} whole-stripe passes "
-                                      f"(encode + 4-erasure decode in each of the 3 realizations); value = mean "
+                                      f"(encode + 4-erasure decode in each of the {len(REALIZATIONS)} realizations); value = mean "
                                       f"over the steps", **cpu_info()}
     return {
         "impl": "reference", "metric": METRIC, "value": round(v, 4), "unit": "GB/s", "n_gpus": world,
