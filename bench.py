@@ -371,10 +371,12 @@ def run_e2e(args, wl, device):
         are decoded and the rebuilt blocks come back (staging_layout).
     Copies are transfers between pinned host memory and the device, inside
     the timed region: host -> device as copy-engine transfers, device ->
-    host by the library's gather kernel (rs_copy_blocks), because on GB300
-    a copy-engine transfer in each direction at once measured 128 GB/s in
-    total, a copy engine one way and the kernel the other 296 GB/s (one
-    direction alone: 211 GB/s host -> device, 193 GB/s device -> host).  Each request stream has its own device and host
+    host through rs_copy_blocks, on a copy engine or by the library's
+    gather kernel, whichever a probe of as many steps after the warm-up
+    measures faster: how the link shares its two directions differs between GB300
+    boxes (engine both ways 128 GB/s in total on one, 343 on another; a
+    copy engine one way and the kernel the other 296 and 289; one direction
+    alone about 211 GB/s host -> device and 193 device -> host).  Each request stream has its own device and host
     buffers (the decode reads the parity stored by the warm-up's encode) and
     works in E2E_CHUNKS chunks of stripes: chunk c's input copy and launch go
     on one CUDA stream, its output copy on a second one, so the host->device
@@ -431,7 +433,7 @@ def run_e2e(args, wl, device):
                               sin=torch.cuda.Stream(device=device), sout=torch.cuda.Stream(device=device)))
         checks.append((real, hp, hout, truth))
 
-    def step():
+    def step(d2h_engine):
         h2d = d2h = 0
         for f in flows:
             for ch in f["chunks"]:
@@ -445,12 +447,11 @@ def run_e2e(args, wl, device):
                     coded.record(f["sin"])
                 f["sout"].wait_event(coded)
                 with torch.cuda.stream(f["sout"]):
-                    # device -> host by the gather kernel, host -> device on
-                    # the copy engines: with both directions busy, one engine
-                    # transfer each way shared the link worst (see the docstring)
+                    # device -> host on a copy engine (one range) or by the
+                    # gather kernel, whichever the probe below measured faster
                     src, dst = f["do"][a:b], f["ho"][a:b]
                     rs.rs_copy_blocks([dst.data_ptr()], [src.data_ptr()], [src.numel()], stream=f["sout"],
-                                      engine_min_bytes=rs.ENGINE_NEVER)
+                                      engine_min_bytes=1 if d2h_engine else rs.ENGINE_NEVER)
                     ch["done"] = torch.cuda.Event()
                     ch["done"].record(f["sout"])
                 h2d += f["di"][a:b].numel()
@@ -464,27 +465,29 @@ def run_e2e(args, wl, device):
                 ev.record(st)
                 main.wait_event(ev)
 
-    start = torch.cuda.Event()
-    start.record(main)
-    for f in flows:
-        f["sin"].wait_event(start)
-        f["sout"].wait_event(start)
-    for _ in range(max(1, args.warmup)):
-        step()
-    join()
-    torch.cuda.synchronize()
-    t0 = torch.cuda.Event(enable_timing=True)
-    t1 = torch.cuda.Event(enable_timing=True)
-    t0.record(main)
-    for f in flows:
-        f["sin"].wait_event(t0)
-        f["sout"].wait_event(t0)
-    for _ in range(args.steps):
-        h2d, d2h = step()
-    join()
-    t1.record(main)
-    torch.cuda.synchronize()
-    ms = t0.elapsed_time(t1)
+    def timed(steps, d2h_engine):
+        t0 = torch.cuda.Event(enable_timing=True)
+        t1 = torch.cuda.Event(enable_timing=True)
+        t0.record(main)
+        for f in flows:
+            f["sin"].wait_event(t0)
+            f["sout"].wait_event(t0)
+        for _ in range(steps):
+            sizes = step(d2h_engine)
+        join()
+        t1.record(main)
+        torch.cuda.synchronize()
+        return t0.elapsed_time(t1), sizes
+
+    # warm-up, then a short probe of the two device -> host paths: how the
+    # host link shares its two directions between copy engines and SM
+    # traffic differs between machines (one GB300 machine: engine both ways 128
+    # GB/s in total, engine + gather kernel 296; another: 343 and 289)
+    timed(max(1, args.warmup), True)
+    nprobe = max(2, args.steps)
+    probe = {mode: timed(nprobe, mode == "copy_engine")[0] for mode in ("copy_engine", "gather_kernel")}
+    d2h_mode = min(probe, key=probe.get)
+    ms, (h2d, d2h) = timed(args.steps, d2h_mode == "copy_engine")
     for real, hp, hout, truth in checks:
         if not torch.equal(hout, truth):
             raise RuntimeError(f"e2e: {real} decode returned wrong blocks")
@@ -495,7 +498,8 @@ def run_e2e(args, wl, device):
             ch["batch"].close()
     step_bytes = len(REALIZATIONS) * 2 * S * (K + M) * BLOCK
     return {"value": round(args.steps * step_bytes / (ms * 1e-3) / 1e9, 2), "unit": "GB/s",
-            "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h}
+            "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h, "d2h_path": d2h_mode,
+            "probe_gbs": {k: round(nprobe * step_bytes / (v * 1e-3) / 1e9, 1) for k, v in probe.items()}}
 
 
 SERVE_LOAD = 0.5      # fraction of the measured saturation rate
