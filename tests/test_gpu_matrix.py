@@ -115,12 +115,16 @@ def test_cauchy_block_size_must_fit_packets(rs):
 
 # Packet-layout tiles are runs of consumer_warps x 32 units (G words of each
 # packet row); these shapes make tiles start inside a super-packet, span
-# several, and end short at the block's end.
+# several, and end short at the block's end.  The GF(2^16) cases with 768-
+# and 256-byte packets run the two-word-per-lane kernels (encodes, good
+# Cauchy decode), 384-byte packets the one-word ones.
 @pytest.mark.parametrize("warps", [1, 3, 5, 12, 16])
 @pytest.mark.parametrize("real,w,k,m,pkt,nsp", [("cauchy", 8, 10, 4, 2048, 7), ("cauchy", 8, 10, 4, 256, 37),
                                                 ("cauchy", 8, 10, 4, 768, 5), ("cauchy", 8, 7, 5, 640, 9),
                                                 ("poly_bitmatrix", 8, 10, 4, 1024, 6),
-                                                ("cauchy", 16, 12, 4, 384, 5), ("good_cauchy", 8, 10, 4, 768, 5)])
+                                                ("cauchy", 16, 12, 4, 384, 5), ("good_cauchy", 8, 10, 4, 768, 5),
+                                                ("cauchy", 16, 12, 4, 768, 3), ("good_cauchy", 16, 12, 4, 768, 3),
+                                                ("good_cauchy", 16, 12, 4, 256, 5)])
 def test_packet_tiles_any_warp_count(rs, real, w, k, m, pkt, nsp, warps):
     import torch
     B = nsp * w * pkt
