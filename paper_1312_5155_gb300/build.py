@@ -67,7 +67,7 @@ def instances():
             for op in (0, 1):
                 key = dict(family=0, w=w, m=m, op=op)
                 out.append((f"poly_w{w}_m{m}_op{op}", f"PolyBody<{w}, {m}, {op}>", key))
-                if op == 1 and w == 8 and m <= 4:
+                if op == 1 and w == 8 and m <= 6:
                     out.append((f"poly_w{w}_m{m}_op{op}_g2", f"PolyDecode2Body<{w}, {m}>", dict(key, wide=1)))
     for w in (8, 16):
         for m in M_RANGE[w]:

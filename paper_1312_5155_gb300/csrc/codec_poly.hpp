@@ -333,12 +333,13 @@ struct PolyDecode {
 
 // apply_and_store for two 32-column groups: output t of group 0 from the
 // syndromes A, of group 1 from B, stored as one 2W-word output (group 0 in
-// words 0..W-1; planes back to symbols with kTranspose).  M <= 4; pair sums
-// with kPairSums.
+// words 0..W-1; planes back to symbols with kTranspose).  Pair sums with
+// kPairSums (M <= 4, one selector chunk); M = 5..8 take a second chunk per
+// coefficient bit.
 template <int W, int M, bool kTranspose = true, bool kPairSums = false, class Dst>
 RS_HD void apply2_and_store(int e, const uint32_t (*A)[W], const uint32_t (*B)[W], const Selectors<W, M>& sel,
                             Dst& dst) {
-  static_assert(M <= 4, "one selector chunk");
+  static_assert(M <= 8 && (M <= 4 || !kPairSums), "two selector chunks, pair sums with one");
   using Sel = Selectors<W, M>;
   // pair sums A0^A1, A2^A3 (and of B) when the kernel has registers for
   // them: a subset of four syndromes is then at most two terms per plane
@@ -368,10 +369,13 @@ RS_HD void apply2_and_store(int e, const uint32_t (*A)[W], const uint32_t (*B)[W
       StaticFor<0, kSteps>::run([&](auto Uu) {
         constexpr int u = decltype(Uu)::value;
         const int c = c0 - u;
+        constexpr int ns0 = M < 4 ? M : 4;
         if constexpr (kPairs)
           fold_and_select2p<W, u + 1, M>(Sel::nibble(row, c), y, y + W, A, B, PA, PB);
         else
-          fold_and_select2<W, u + 1, M>(Sel::nibble(row, c), y, y + W, A, B);
+          fold_and_select2<W, u + 1, ns0>(Sel::nibble(row, c * Sel::kChunks), y, y + W, A, B);
+        if constexpr (Sel::kChunks > 1)
+          xor_selected2<W, u + 1, M - 4>(Sel::nibble(row, c * Sel::kChunks + 1), y, y + W, A + 4, B + 4);
       });
       if constexpr (kSteps % W != 0) {
         uint32_t r[2 * W];
@@ -398,10 +402,10 @@ RS_HD void apply2_and_store(int e, const uint32_t (*A)[W], const uint32_t (*B)[W
 // barrier waits, the selector dispatch -- then serves 64 columns, and the
 // two groups' instruction streams are independent.  Pair sums in the
 // decode-matrix step with kPairSums (they need the larger register budget
-// of the split kernel); M <= 4.
+// of the split kernel; M <= 4); M = 5..8 without.
 template <int W, int M, bool kPairSums = false>
 struct PolyDecode2 {
-  static_assert(M <= 4, "one selector chunk");
+  static_assert(M <= 8 && (M <= 4 || !kPairSums), "pair sums with one selector chunk");
   template <class Src, class Dst, class Coef>
   static RS_HD void run(int n_pos, uint64_t read_mask, int e, Src& src, Dst& dst, Coef& coef) {
     Selectors<W, M> sel;

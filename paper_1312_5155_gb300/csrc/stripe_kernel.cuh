@@ -413,15 +413,16 @@ struct PolyDecode2Body : SymbolDecodeSplit {
   static constexpr int kGroups = 2;
   static constexpr int kLayout = kLayoutSymbol;
   static constexpr int kMaxOut = M;
-  // two groups of syndromes and outputs live at once, plus the pair sums:
-  // 12 consumer warps at the split's 152 registers
+  // two groups of syndromes and outputs live at once, plus the pair sums
+  // for m <= 4 (m = 5, 6: two selector chunks, no pair sums): 12 consumer
+  // warps at the split's 152 registers
   static constexpr int kMaxWarps = kSplitMaxConsumers;
   static constexpr int kMinBlocks = 1;
   __device__ static bool matches(const TileOp& o) { return o.op == kOpDecode && o.m == M; }
   template <class Tile>
   __device__ static void run(const TileOp& o, Tile& t, const uint32_t* coef) {
     CoefWords cm{coef};
-    PolyDecode2<W, M, true>::run(o.n_pos, o.read_mask, o.e, t, t, cm);
+    PolyDecode2<W, M, (M <= 4)>::run(o.n_pos, o.read_mask, o.e, t, t, cm);
   }
 };
 

@@ -121,7 +121,7 @@ void run_decode2(const DecodePlan& pl, uint8_t* blocks, size_t B) {
   for (size_t seg = 0; seg < B; seg += segb)
     for (int lane = 0; lane < 32; ++lane) {
       HostTileG<W, 2> t{in.data(), out.data(), B, seg, lane};
-      PolyDecode2<W, M, true>::run(pl.n_pos, pl.read_mask, pl.e, t, t, cf);  // pair sums, as the kernel
+      PolyDecode2<W, M, (M <= 4)>::run(pl.n_pos, pl.read_mask, pl.e, t, t, cf);  // pair sums for M <= 4, as the kernel
     }
 }
 
@@ -612,6 +612,8 @@ int emu_poly_decode2(int w, int k, int m, const int* er, int e, int read_all, ui
     case 2: run_decode2<8, 2>(pl, blocks, B); return 0;
     case 3: run_decode2<8, 3>(pl, blocks, B); return 0;
     case 4: run_decode2<8, 4>(pl, blocks, B); return 0;
+    case 5: run_decode2<8, 5>(pl, blocks, B); return 0;
+    case 6: run_decode2<8, 6>(pl, blocks, B); return 0;
   }
   return -2;
 }

@@ -101,7 +101,8 @@ def decode_case(rs, w, k, m, B, er, read_mode, seed=2, stripe=0):
 @pytest.mark.parametrize("read_mode", [0, 1])
 @pytest.mark.parametrize("w,k,m,B", [(8, 10, 4, 65536 + 16), (8, 6, 3, 5000), (16, 12, 4, 40002),
                                      (8, 20, 4, 100000), (8, 10, 8, 9000), (8, 10, 4, (1 << 18) + 37),
-                                     (8, 6, 3, 300001), (8, 12, 4, 1 << 19)])
+                                     (8, 6, 3, 300001), (8, 12, 4, 1 << 19), (8, 10, 5, (1 << 18) + 48),
+                                     (8, 10, 6, 300000 + 16)])
 def test_decode_seeded_patterns(rs, w, k, m, B, read_mode):
     n = k + m
     seed = inputs.stream_seed(2)

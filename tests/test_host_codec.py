@@ -117,9 +117,10 @@ def test_decode_seeded_patterns_match_oracle(emu, w, k, m, read_all):
 
 @pytest.mark.parametrize("read_all", [False, True])
 @pytest.mark.parametrize("k,m,B", [(10, 4, 4096 + 48), (6, 3, 3000), (12, 4, 2048 + 7), (5, 2, 2048),
-                                   (20, 4, 9000), (3, 1, 100)])
+                                   (20, 4, 9000), (3, 1, 100), (10, 5, 3000), (10, 6, 2048 + 9)])
 def test_two_group_decode_matches_oracle(emu, k, m, B, read_all):
-    """The decode with two 32-column groups per thread (GF(2^8), M <= 4)."""
+    """The decode with two 32-column groups per thread (GF(2^8), M <= 6;
+    two selector chunks for M = 5, 6)."""
     emu.emu_poly_decode2.argtypes = [ctypes.c_int] * 3 + [ctypes.POINTER(ctypes.c_int), ctypes.c_int,
                                                           ctypes.c_int, U8P, ctypes.c_size_t]
     w, n = 8, k + m
@@ -135,7 +136,7 @@ def test_two_group_decode_matches_oracle(emu, k, m, B, read_all):
         got[list(er)] = 0x5A
         arr = (ctypes.c_int * len(er))(*er)
         rc = emu.emu_poly_decode2(w, k, m, arr, len(er), int(read_all), got.ctypes.data_as(U8P), B)
-        if rc == -2:  # M > 4 (read-all with fewer erasures keeps M <= e)
+        if rc == -2:  # M > 6
             continue
         assert rc == 0
         assert np.array_equal(got, base), er
