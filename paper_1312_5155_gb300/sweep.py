@@ -352,7 +352,8 @@ def mixed_batch_ops(seed, shapes, views, code):
 def kmsweep(points=None):
     """§5.2 Fig. 3 and 4 on the GPU.  Every matrix realization runs a
     compiled generator at every point when the library was built with
-    RSGB_BUILD_KM_CODES=1 (`compiled_generator` in each line says which)."""
+    RSGB_BUILD_KM_CODES=1; `compiled_generator` in each line reads the same
+    variable, so set it for the sweep as for the build."""
     from . import build
     compiled = set(build.fixed_codes())
     seed = inputs.workload_seed("block_sizes")
