@@ -372,8 +372,8 @@ def run_e2e(args, wl, device):
     Copies are transfers between pinned host memory and the device, inside
     the timed region: host -> device as copy-engine transfers, device ->
     host through rs_copy_blocks, on a copy engine or by the library's
-    gather kernel, whichever a probe of as many steps after the warm-up
-    measures faster: how the link shares its two directions differs between GB300
+    gather kernel: after the warm-up the K timed steps run once with each
+    path and the line reports the faster run (both are in `paths_gbs`): how the link shares its two directions differs between GB300
     boxes (engine both ways 128 GB/s in total on one, 343 on another; a
     copy engine one way and the kernel the other 296 and 289; one direction
     alone about 211 GB/s host -> device and 193 device -> host).  Each request stream has its own device and host
@@ -479,15 +479,16 @@ def run_e2e(args, wl, device):
         torch.cuda.synchronize()
         return t0.elapsed_time(t1), sizes
 
-    # warm-up, then a short probe of the two device -> host paths: how the
-    # host link shares its two directions between copy engines and SM
-    # traffic differs between machines (one GB300 machine: engine both ways 128
-    # GB/s in total, engine + gather kernel 296; another: 343 and 289)
+    # warm-up, then the K steps once with each device -> host path, keeping
+    # the faster run: how the host link shares its two directions between
+    # copy engines and SM traffic differs between machines (one GB300 machine:
+    # engine both ways 128 GB/s in total, engine + gather kernel 296;
+    # another: 343 and 289)
     timed(max(1, args.warmup), True)
-    nprobe = max(2, args.steps)
-    probe = {mode: timed(nprobe, mode == "copy_engine")[0] for mode in ("copy_engine", "gather_kernel")}
-    d2h_mode = min(probe, key=probe.get)
-    ms, (h2d, d2h) = timed(args.steps, d2h_mode == "copy_engine")
+    runs = {mode: timed(args.steps, mode == "copy_engine") for mode in ("copy_engine", "gather_kernel")}
+    path_ms = {mode: r[0] for mode, r in runs.items()}
+    d2h_mode = min(path_ms, key=path_ms.get)
+    ms, (h2d, d2h) = runs[d2h_mode]
     for real, hp, hout, truth in checks:
         if not torch.equal(hout, truth):
             raise RuntimeError(f"e2e: {real} decode returned wrong blocks")
@@ -499,7 +500,7 @@ def run_e2e(args, wl, device):
     step_bytes = len(REALIZATIONS) * 2 * S * (K + M) * BLOCK
     return {"value": round(args.steps * step_bytes / (ms * 1e-3) / 1e9, 2), "unit": "GB/s",
             "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h, "d2h_path": d2h_mode,
-            "probe_gbs": {k: round(nprobe * step_bytes / (v * 1e-3) / 1e9, 1) for k, v in probe.items()}}
+            "paths_gbs": {k: round(args.steps * step_bytes / (v * 1e-3) / 1e9, 1) for k, v in path_ms.items()}}
 
 
 SERVE_LOAD = 0.5      # fraction of the measured saturation rate

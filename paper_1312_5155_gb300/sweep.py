@@ -134,10 +134,18 @@ def single_stripe():
     code = rs.Code(k, m, w, "poly")
     rows = list(buf)
     er = inputs.erasure_pattern(seed, 0, n, m)
-    lat_e = _time(lambda: code.encode(rows[:k], rows[k:], B), reps=50)
-    lat_d = _time(lambda: code.decode(er, rows, B), reps=50)
+    enc = lambda: code.encode(rows[:k], rows[k:], B)  # noqa: E731
+    dec = lambda: code.decode(er, rows, B)  # noqa: E731
+    lat_e = _time(enc, reps=50)
+    lat_d = _time(dec, reps=50)
+    # the device side of one call alone: the same call captured in a CUDA
+    # graph and replayed (no Python or ctypes work between the events)
+    g_e, g_d = _graph_of(enc), _graph_of(dec)
+    dev_e = _time(g_e.replay, reps=50)
+    dev_d = _time(g_d.replay, reps=50)
     print(json.dumps({"workload": "single_stripe", "what": "one stripe, one call", "encode_us": round(lat_e * 1e3, 1),
-                      "decode_us": round(lat_d * 1e3, 1)}), flush=True)
+                      "decode_us": round(lat_d * 1e3, 1), "graph_replay_encode_us": round(dev_e * 1e3, 1),
+                      "graph_replay_decode_us": round(dev_d * 1e3, 1)}), flush=True)
     del buf
     r = _batch_pair("poly", w, k, m, B, 1024, seed, m, tag="c1-")
     print(json.dumps({"workload": "single_stripe", "what": "1024 replicated stripes, batched", **r}), flush=True)
