@@ -185,8 +185,9 @@ typedef struct {
 
 /* Create a batch able to hold up to max_ops operations (1..2^20).
  * Allocates its device descriptor tables and a pinned staging buffer on
- * the current device (about 4.7 KB per op).  Errors: RS_EINVAL, RS_ENOMEM,
- * RS_ECUDA. */
+ * the current device (about 4.7 KB per op), and the side streams and
+ * events that rs_batch_launch runs its kernel groups on.  Errors:
+ * RS_EINVAL, RS_ENOMEM, RS_ECUDA. */
 rs_status rs_batch_create(int max_ops, rs_batch **out);
 
 /* Free a batch (NULL is ignored); its launches must have completed. */
