@@ -152,3 +152,45 @@ def test_batch_mixes_one_and_two_group_kernels(rs):
     assert b.poll_status() == 0
     check(items)
     assert b.kernel_count >= 4
+
+
+def test_multi_group_batch_orders_later_work_on_its_stream(rs):
+    """The kernel groups after the first run on the batch's side streams;
+    work queued on the launch stream after rs_batch_launch (here copies of
+    every output block, taken without any host synchronisation) must see
+    all groups finished, eagerly and through a captured graph."""
+    import torch
+    specs = []
+    for i in range(3):
+        specs += [("poly", 8, 10, 4, 1 << 20, None, "encode", 0),
+                  ("vandermonde", 8, 10, 4, 1 << 20, None, "encode", 0),
+                  ("good_cauchy", 8, 10, 4, 8 * 2048 * 64, 2048, "decode", 1 + i),
+                  ("poly", 8, 6, 3, 1 << 20, None, "decode", 1 + i)]
+    codes, items = make_workload(rs, specs, seed=0x5EED0009)
+    b = rs.Batch(len(items))
+    s = torch.cuda.Stream()
+    s.wait_stream(torch.cuda.current_stream())
+    with torch.cuda.stream(s):
+        b.set([(it["code"], it["op"], it["er"], it["rows"], it["B"]) for it in items], stream=s)
+        assert b.kernel_count >= 3
+        b.launch(stream=s)
+        snaps = [it["buf"].clone() for it in items]
+    torch.cuda.synchronize()
+    assert b.poll_status() == 0
+    for it, snap in zip(items, snaps):
+        assert np.array_equal(snap[:, :it["B"]].cpu().numpy(), it["ref"]), (it["op"], it["code"].realization)
+    # the same through a graph: reset the blocks, replay, copy on the stream
+    for it in items:
+        it["buf"][:, :it["B"]] = torch.from_numpy(it["start"]).cuda()
+    torch.cuda.synchronize()
+    with torch.cuda.stream(s):
+        g = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(g, stream=s):
+            b.launch(stream=s)
+        for it in items:
+            it["buf"][:, :it["B"]] = torch.from_numpy(it["start"]).cuda()
+        g.replay()
+        snaps = [it["buf"].clone() for it in items]
+    torch.cuda.synchronize()
+    for it, snap in zip(items, snaps):
+        assert np.array_equal(snap[:, :it["B"]].cpu().numpy(), it["ref"]), (it["op"], it["code"].realization, "graph")
