@@ -284,7 +284,8 @@ rs_status rs_copy_blocks(void *const *dst, const void *const *src, const size_t 
  * Set-up: the first call on a device looks up the array's device address
  * (cudaGetSymbolAddress, with that device current), and the first call for
  * each (w, m) on a device sets its encode kernel's shared-memory size
- * attribute; later calls skip both steps.  The array
+ * attribute; later calls skip both steps.  Make those first calls before
+ * any stream capture begins.  The array
  * is shared by all calls on a device and keeps the last call's contents:
  * each call clears the status word and rewrites the tables before its
  * kernel runs, so calls whose work overlaps on the GPU race -- order them
