@@ -105,6 +105,15 @@ rs_status rs_set_read_mode(rs_code *code, int mode);
  * (1..4).  0 keeps the current value.  Set by the autotuner. */
 rs_status rs_set_launch(rs_code *code, int consumer_warps, int depth, int ctas_per_sm);
 
+/* Columns per thread of this code's kernels (not in the paper): 0 (the
+ * default) picks the two-group kernels, 64 columns per thread, from blocks
+ * of 256 KiB (symbol layout) or 8 KiB (packet layout) where they are
+ * compiled; 1 always takes the one-group kernels (32 columns); 2 takes the
+ * two-group kernels at every block size where they are compiled (else the
+ * one-group ones).  Read when an encode or decode is prepared.  Set by the
+ * autotuner.  Errors: RS_EINVAL. */
+rs_status rs_set_groups(rs_code *code, int groups);
+
 /* Encode one stripe: parity from data.  §3.2 Eq. 1 (polynomial: remainder of
  * x^m d(x) divided by g(x)), §2.1 (matrix: parity rows of G times d).
  *   data_ptrs: host array of k device pointers (read only);
@@ -195,6 +204,10 @@ void rs_batch_destroy(rs_batch *batch);
 
 /* Launch shape for the batch's kernels (as rs_set_launch). */
 rs_status rs_batch_set_launch(rs_batch *batch, int consumer_warps, int depth, int ctas_per_sm);
+
+/* Columns per thread for the batch's ops (as rs_set_groups; the batch's
+ * setting, not the codes', applies); read by rs_batch_set. */
+rs_status rs_batch_set_groups(rs_batch *batch, int groups);
 
 /* Validate and plan n_ops operations (§3.2 / §3.3 / §2.1 per op, as in
  * rs_encode / rs_decode), group them by kernel (at most 8 groups), and

@@ -1,6 +1,7 @@
 """Launch-shape autotuner for the stripe kernels.
 
-A launch shape is (consumer warps per CTA, ring depth, CTAs per SM):
+A launch shape is (consumer warps per CTA, ring depth, CTAs per SM[,
+columns per thread]):
   - consumer warps set the tile width: a tile covers consumer_warps x 32
     threads x 32 columns of every block (1 KiB per warp at w = 8,
     2 KiB at w = 16), and every thread owns 32 columns (64 in the
@@ -8,7 +9,9 @@ A launch shape is (consumer warps per CTA, ring depth, CTAs per SM):
     allow;
   - ring depth is how many block slices are in flight per CTA (the unroll
     depth of the shared-memory pipeline);
-  - CTAs per SM sets the persistent grid (SMs x CTAs per SM).
+  - CTAs per SM sets the persistent grid (SMs x CTAs per SM);
+  - columns per thread: one or two groups of 32 (the kernels' G); absent =
+    the library's choice by block size.
 The tuner times every candidate shape on the device (CUDA events, after
 warm-up) for one batch and keeps the fastest.  Results are cached in a JSON
 file keyed by (op, realization, k, m, w, block-size bucket, SM count).
@@ -69,10 +72,14 @@ def time_launch(launch, reps: int = 5, warmup: int = 2) -> float:
     return e0.elapsed_time(e1) / reps
 
 
-def tune_batch(batch, ops, key: str | None = None, candidates=None, reps: int = 5, use_cache: bool = True):
+def tune_batch(batch, ops, key: str | None = None, candidates=None, reps: int = 5, use_cache: bool = True,
+               group_search: bool = True):
     """Pick the fastest launch shape for `batch` running `ops` (the list
-    given to Batch.set).  Leaves the batch set with the winning shape and
-    returns (shape, {shape: ms})."""
+    given to Batch.set): every candidate (warps, depth, CTAs per SM) with
+    the columns per thread chosen by block size, then the two best with one
+    and with two 32-column groups forced (a fourth element of the shape).
+    Leaves the batch set with the winning shape and returns (shape,
+    {shape: ms})."""
     candidates = list(candidates or CANDIDATES)
     if key and use_cache:
         with _lock:
@@ -87,6 +94,17 @@ def tune_batch(batch, ops, key: str | None = None, candidates=None, reps: int = 
         batch.set_launch(*shape)
         batch.set(ops)
         results[shape] = time_launch(batch.launch, reps=reps)
+    # columns per thread: the two best shapes again with one and with two
+    # 32-column groups per thread forced (the default picks by block size)
+    if group_search:
+        for shape in sorted(results, key=results.get)[:2]:
+            if len(shape) > 3:
+                continue
+            for g in (1, 2):
+                s4 = tuple(shape) + (g,)
+                batch.set_launch(*s4)
+                batch.set(ops)
+                results[s4] = time_launch(batch.launch, reps=reps)
     best = min(results, key=results.get)
     batch.set_launch(*best)
     batch.set(ops)

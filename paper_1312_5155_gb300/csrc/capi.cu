@@ -164,7 +164,9 @@ struct PreparedOp {
 constexpr size_t kWideSymbolMinBytes = 256u << 10;
 constexpr size_t kWidePacketMinBytes = 8u << 10;
 
-rs_status select_kernel(const rs_code* c, int op, int M, size_t B, PreparedOp& po) {
+// groups: 0 = the two-group kernel from the thresholds above, 1 = the
+// one-group kernel, 2 = the two-group kernel whenever one is compiled.
+rs_status select_kernel(const rs_code* c, int op, int M, size_t B, PreparedOp& po, int groups) {
   KernelKey key;
   key.w = c->w;
   key.m = M;
@@ -183,7 +185,8 @@ rs_status select_kernel(const rs_code* c, int op, int M, size_t B, PreparedOp& p
     }
   }
   po.entry = nullptr;
-  if (B >= (key.layout == kLayoutPacket ? kWidePacketMinBytes : kWideSymbolMinBytes)) {
+  const size_t wide_min = key.layout == kLayoutPacket ? kWidePacketMinBytes : kWideSymbolMinBytes;
+  if (groups == 2 || (groups == 0 && B >= wide_min)) {
     key.wide = 1;
     po.entry = find_kernel(key);
     // a packet kernel's tiles are whole warps of units (G 32-bit words of
@@ -206,14 +209,15 @@ void fill_common(const rs_code* c, size_t B, StripeDesc& d) {
   d.pmask = (uint64_t)(uintptr_t)c->d_pmask;
 }
 
-rs_status prepare_encode(rs_code* c, const void* const* data, void* const* parity, size_t B, PreparedOp& po) {
+rs_status prepare_encode(rs_code* c, const void* const* data, void* const* parity, size_t B, PreparedOp& po,
+                         int groups) {
   if (!data || !parity) return fail(RS_EINVAL, "pointer array is null");
   std::vector<const void*> all;
   for (int i = 0; i < c->k; ++i) all.push_back(data[i]);
   for (int j = 0; j < c->m; ++j) all.push_back(parity[j]);
   rs_status s = check_blocks(c, all, B);
   if (s != RS_OK) return s;
-  if ((s = select_kernel(c, kOpEncode, c->m, B, po)) != RS_OK) return s;
+  if ((s = select_kernel(c, kOpEncode, c->m, B, po, groups)) != RS_OK) return s;
   po.noop = B == 0;
   StripeDesc& d = po.d;
   fill_common(c, B, d);
@@ -272,7 +276,8 @@ rs_status prepare_update(rs_code* c, int index, const void* delta, void* const* 
   return RS_OK;
 }
 
-rs_status prepare_decode(rs_code* c, const int* er, int e, void* const* blocks, size_t B, PreparedOp& po) {
+rs_status prepare_decode(rs_code* c, const int* er, int e, void* const* blocks, size_t B, PreparedOp& po,
+                         int groups) {
   if (e < 0) return fail(RS_EINVAL, "negative erasure count");
   if (e > c->m) return fail(RS_ETOOMANY_ERASURES, "more erasures than parity blocks");
   if (e > 0 && !er) return fail(RS_EINVAL, "erasure list is null");
@@ -286,7 +291,7 @@ rs_status prepare_decode(rs_code* c, const int* er, int e, void* const* blocks, 
   if ((s = get_plan(c, er, e, pl)) != RS_OK) return s;
   po.noop = e == 0 || B == 0;
   if (e == 0) return RS_OK;
-  if ((s = select_kernel(c, kOpDecode, pl.M, B, po)) != RS_OK) return s;
+  if ((s = select_kernel(c, kOpDecode, pl.M, B, po, groups)) != RS_OK) return s;
   StripeDesc& d = po.d;
   fill_common(c, B, d);
   d.read_mask = pl.read_mask;
@@ -576,11 +581,18 @@ rs_status rs_set_launch(rs_code* c, int consumer_warps, int depth, int ctas_per_
   return set_tune(c->tune, consumer_warps, depth, ctas_per_sm);
 }
 
+rs_status rs_set_groups(rs_code* c, int groups) {
+  if (!c) return fail(RS_EINVAL, "code is null");
+  if (groups < 0 || groups > 2) return fail(RS_EINVAL, "groups must be 0, 1 or 2");
+  c->tune.groups = groups;
+  return ok();
+}
+
 rs_status rs_encode(rs_code* c, const void* const* data_ptrs, void* const* parity_ptrs, size_t block_bytes,
                     void* stream) {
   if (!c) return fail(RS_EINVAL, "code is null");
   PreparedOp po;
-  rs_status s = prepare_encode(c, data_ptrs, parity_ptrs, block_bytes, po);
+  rs_status s = prepare_encode(c, data_ptrs, parity_ptrs, block_bytes, po, c->tune.groups);
   if (s != RS_OK) return s;
   return launch_single(c, po, stream);
 }
@@ -589,7 +601,7 @@ rs_status rs_decode(rs_code* c, const int* erasures, int n_erasures, void* const
                     void* stream) {
   if (!c) return fail(RS_EINVAL, "code is null");
   PreparedOp po;
-  rs_status s = prepare_decode(c, erasures, n_erasures, block_ptrs, block_bytes, po);
+  rs_status s = prepare_decode(c, erasures, n_erasures, block_ptrs, block_bytes, po, c->tune.groups);
   if (s != RS_OK) return s;
   return launch_single(c, po, stream);
 }
@@ -676,6 +688,13 @@ rs_status rs_batch_set_launch(rs_batch* b, int consumer_warps, int depth, int ct
   return set_tune(b->tune, consumer_warps, depth, ctas_per_sm);
 }
 
+rs_status rs_batch_set_groups(rs_batch* b, int groups) {
+  if (!b) return fail(RS_EINVAL, "batch is null");
+  if (groups < 0 || groups > 2) return fail(RS_EINVAL, "groups must be 0, 1 or 2");
+  b->tune.groups = groups;
+  return ok();
+}
+
 rs_status rs_batch_set(rs_batch* b, const rs_op* ops, int n_ops, void* stream) {
   if (!b) return fail(RS_EINVAL, "batch is null");
   if (n_ops < 0 || n_ops > b->max_ops) return fail(RS_EINVAL, "n_ops out of range");
@@ -690,9 +709,9 @@ rs_status rs_batch_set(rs_batch* b, const rs_op* ops, int n_ops, void* stream) {
     if (o.code->device != b->device) return fail(RS_EINVAL, "op " + std::to_string(i) + ": code on another device");
     if (o.op == RS_OP_ENCODE)
       s = prepare_encode(o.code, (const void* const*)o.blocks, (void* const*)(o.blocks + o.code->k), o.block_bytes,
-                         prep[i]);
+                         prep[i], b->tune.groups);
     else if (o.op == RS_OP_DECODE)
-      s = prepare_decode(o.code, o.erasures, o.n_erasures, o.blocks, o.block_bytes, prep[i]);
+      s = prepare_decode(o.code, o.erasures, o.n_erasures, o.blocks, o.block_bytes, prep[i], b->tune.groups);
     else
       s = fail(RS_EINVAL, "unknown op kind");
     if (s != RS_OK) return fail(s, "op " + std::to_string(i) + ": " + g_last_error);

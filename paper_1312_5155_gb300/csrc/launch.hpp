@@ -22,6 +22,7 @@ struct TuneCfg {
   int consumer_warps = 8;  // NC
   int depth = 16;          // ring slots
   int ctas_per_sm = 1;
+  int groups = 0;          // 32-column groups per thread: 0 = by block size, 1, or 2 where compiled
 };
 
 // Thread-local message behind rs_last_error (set on failure, cleared on

@@ -63,6 +63,7 @@ def lib() -> ctypes.CDLL:
                 "rs_set_packet_bytes": (ctypes.c_int, [VP, ctypes.c_size_t]),
                 "rs_set_read_mode": (ctypes.c_int, [VP, ctypes.c_int]),
                 "rs_set_launch": (ctypes.c_int, [VP, ctypes.c_int, ctypes.c_int, ctypes.c_int]),
+                "rs_set_groups": (ctypes.c_int, [VP, ctypes.c_int]),
                 "rs_encode": (ctypes.c_int, [VP, ctypes.POINTER(VP), ctypes.POINTER(VP), ctypes.c_size_t, VP]),
                 "rs_decode": (ctypes.c_int, [VP, ctypes.POINTER(ctypes.c_int), ctypes.c_int,
                                              ctypes.POINTER(VP), ctypes.c_size_t, VP]),
@@ -80,6 +81,7 @@ def lib() -> ctypes.CDLL:
                 "rs_batch_create": (ctypes.c_int, [ctypes.c_int, ctypes.POINTER(VP)]),
                 "rs_batch_destroy": (None, [VP]),
                 "rs_batch_set_launch": (ctypes.c_int, [VP, ctypes.c_int, ctypes.c_int, ctypes.c_int]),
+                "rs_batch_set_groups": (ctypes.c_int, [VP, ctypes.c_int]),
                 "rs_batch_set": (ctypes.c_int, [VP, ctypes.POINTER(RsOp), ctypes.c_int, VP]),
                 "rs_batch_launch": (ctypes.c_int, [VP, VP]),
                 "rs_batch_kernel_count": (ctypes.c_int, [VP]),
@@ -151,6 +153,10 @@ def rs_set_launch(handle: int, consumer_warps: int = 0, depth: int = 0, ctas_per
     _check(lib().rs_set_launch(handle, consumer_warps, depth, ctas_per_sm))
 
 
+def rs_set_groups(handle: int, groups: int) -> None:
+    _check(lib().rs_set_groups(handle, groups))
+
+
 def rs_encode(handle: int, data, parity, block_bytes: int, stream=None) -> None:
     _check(lib().rs_encode(handle, _ptr_array(data), _ptr_array(parity), block_bytes, _stream(stream)))
 
@@ -194,8 +200,12 @@ class Code:
     def n(self) -> int:
         return self.k + self.m
 
-    def set_launch(self, consumer_warps=0, depth=0, ctas_per_sm=0):
+    def set_launch(self, consumer_warps=0, depth=0, ctas_per_sm=0, groups=None):
+        """Launch shape; groups (columns per thread: 0 by block size, 1 or
+        2) if given."""
         rs_set_launch(self.handle, consumer_warps, depth, ctas_per_sm)
+        if groups is not None:
+            rs_set_groups(self.handle, groups)
 
     def encode(self, data, parity, block_bytes: int | None = None, stream=None):
         """data: k uint8 device tensors (or a (k, B) tensor); parity: m tensors / (m, B)."""
@@ -245,6 +255,10 @@ def rs_batch_destroy(handle: int) -> None:
 
 def rs_batch_set_launch(handle: int, consumer_warps: int = 0, depth: int = 0, ctas_per_sm: int = 0) -> None:
     _check(lib().rs_batch_set_launch(handle, consumer_warps, depth, ctas_per_sm))
+
+
+def rs_batch_set_groups(handle: int, groups: int) -> None:
+    _check(lib().rs_batch_set_groups(handle, groups))
 
 
 def make_ops(ops):
@@ -299,8 +313,11 @@ class Batch:
         self.handle = rs_batch_create(max_ops)
         self._codes = []
 
-    def set_launch(self, consumer_warps=0, depth=0, ctas_per_sm=0):
+    def set_launch(self, consumer_warps=0, depth=0, ctas_per_sm=0, groups=0):
+        """Launch shape (consumer warps, ring depth, CTAs per SM) and columns
+        per thread (0 by block size, 1 or 2 groups) of the next set()."""
         rs_batch_set_launch(self.handle, consumer_warps, depth, ctas_per_sm)
+        rs_batch_set_groups(self.handle, groups)
 
     def set(self, ops, stream=None):
         ops = list(ops)

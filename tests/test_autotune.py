@@ -23,12 +23,15 @@ class FakeBatch:
 def test_picks_fastest_and_caches(tmp_path, monkeypatch):
     monkeypatch.setenv("RS_GB300_TUNE_CACHE", str(tmp_path / "tune.json"))
     cost = {(16, 8, 1): 3.0, (8, 8, 2): 1.5, (4, 16, 2): 2.0}
+    # the two best shapes are tried again with one and two column groups;
+    # forcing one group is slower, forcing two no faster than the default
+    forced = {(8, 8, 2, 1): 2.5, (8, 8, 2, 2): 1.5, (4, 16, 2, 1): 2.4, (4, 16, 2, 2): 2.0}
     b = FakeBatch(cost)
-    monkeypatch.setattr(autotune, "time_launch", lambda launch, reps=5: cost[b.shape])
+    monkeypatch.setattr(autotune, "time_launch", lambda launch, reps=5: {**cost, **forced}[b.shape])
     key = autotune.make_key("encode", "poly", 10, 4, 8, 1 << 20, 152)
     best, res = autotune.tune_batch(b, [], key=key, candidates=list(cost))
     assert best == (8, 8, 2) and b.shape == (8, 8, 2)
-    assert set(res) == set(cost)
+    assert set(res) == set(cost) | set(forced)
     d = json.loads((tmp_path / "tune.json").read_text())
     assert d[key]["shape"] == [8, 8, 2]
     # second call: cache hit, no timing
@@ -43,3 +46,18 @@ def test_key_buckets_block_sizes():
     k2 = autotune.make_key("decode", "cauchy", 10, 4, 8, (1 << 20) + 4096, 152)
     k3 = autotune.make_key("decode", "cauchy", 10, 4, 8, 1 << 21, 152)
     assert k1 == k2 != k3
+
+
+def test_column_groups_can_win(tmp_path, monkeypatch):
+    """A forced column-group count that beats the default is kept, with the
+    group count as the shape's fourth element."""
+    monkeypatch.setenv("RS_GB300_TUNE_CACHE", str(tmp_path / "tune.json"))
+    cost = {(16, 8, 1): 3.0, (8, 8, 2): 1.5, (4, 16, 2): 2.0,
+            (8, 8, 2, 1): 1.7, (8, 8, 2, 2): 1.2, (4, 16, 2, 1): 2.2, (4, 16, 2, 2): 2.1}
+    b = FakeBatch(cost)
+    monkeypatch.setattr(autotune, "time_launch", lambda launch, reps=5: cost[b.shape])
+    key = autotune.make_key("decode", "poly", 10, 4, 8, 64 << 10, 152)
+    best, _ = autotune.tune_batch(b, [], key=key, candidates=[(16, 8, 1), (8, 8, 2), (4, 16, 2)])
+    assert best == (8, 8, 2, 2) and b.shape == (8, 8, 2, 2)
+    d = json.loads((tmp_path / "tune.json").read_text())
+    assert d[key]["shape"] == [8, 8, 2, 2]

@@ -165,3 +165,35 @@ def test_good_cauchy_has_fewer_ones_and_differs_from_cauchy(rs):
     rs.Code(k, m, w, "good_cauchy", packet_bytes=pkt).encode(b_rows[:k], b_rows[k:], B)
     torch.cuda.synchronize()
     assert torch.equal(a_buf[:k], b_buf[:k]) and not torch.equal(a_buf[k:], b_buf[k:])
+
+
+@pytest.mark.parametrize("groups", [1, 2])
+@pytest.mark.parametrize("real,w,k,m,B,pkt", [("poly", 8, 10, 4, (64 << 10) + 16, None),
+                                              ("vandermonde", 8, 10, 4, (64 << 10) + 16, None),
+                                              ("vandermonde", 8, 6, 3, 1 << 20, None),
+                                              ("poly", 8, 10, 5, 100000, None),
+                                              ("good_cauchy", 8, 10, 4, 8 * 2048 * 3, 2048),
+                                              ("good_cauchy", 16, 12, 4, 16 * 2048, 2048)])
+def test_forced_column_groups_match_oracle(rs, real, w, k, m, B, pkt, groups):
+    """One or two 32-column groups per thread forced on either side of the
+    block-size threshold give the oracle's bytes (encode, then a decode of
+    m seeded erasures)."""
+    import torch
+    code = rs.Code(k, m, w, real, packet_bytes=pkt)
+    code.set_launch(groups=groups)
+    host = stripe(w, k, m, B, seed=13)
+    ref = host.copy()
+    O.encode(real, w, k, m, ref, packet_bytes=pkt or 2048)
+    buf, rows = device_blocks(host)
+    buf[k:] = 0x5A
+    code.encode(rows[:k], rows[k:], B)
+    torch.cuda.synchronize()
+    assert np.array_equal(to_host(buf, B), ref)
+    er = inputs.erasure_pattern(inputs.stream_seed(5), groups, k + m, m)
+    bad = ref.copy()
+    bad[er] = 0xC3
+    buf, rows = device_blocks(bad)
+    code.decode(er, rows, B)
+    torch.cuda.synchronize()
+    assert np.array_equal(to_host(buf, B), ref), er
+    assert code.poll_status() == 0
