@@ -49,6 +49,8 @@ def test_argument_errors_need_no_gpu(library):
     assert L.rs_init(60, 9, 8, 0, ctypes.byref(h)) == 6  # m > 8: unsupported
     assert L.rs_init(10, 4, 8, 9, ctypes.byref(h)) == 1  # realization
     assert L.rs_encode(None, None, None, 0, None) == 1
+    assert L.rs_set_groups(None, 1) == 1
+    assert L.rs_batch_set_groups(None, 2) == 1
     assert L.rs_version() >= 100
 
 
