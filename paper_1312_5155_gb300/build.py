@@ -85,10 +85,11 @@ def instances():
             out.append((name, f"MatFixedBody<{w}, {k}, {m}, {kind}, {op}>", key))
             # GF(2^8) codes with m <= 4 also get two column groups per lane
             # (decodes in both layouts, symbol-layout encodes; the LFSR encode
-            # keeps one).  In the symbol layout only up to k = 12: the unrolled
-            # per-input code of two groups at k = 20 overflows the
-            # instruction cache (encode 4175 -> 2747 GB/s).
-            if w == 8 and m <= 4 and (layout == 1 or k <= 12):
+            # keeps one).  In the symbol layout only up to k = 16: beyond,
+            # the unrolled per-input code of two groups outgrows the
+            # instruction cache (Vandermonde decode at k = 18..20 4-6 %
+            # slower than one group; at k = 13..16 it is 9-15 % faster).
+            if w == 8 and m <= 4 and (layout == 1 or k <= 16):
                 if op == 3:
                     out.append((name + "_g2", f"MatFixedDecode2Body<{w}, {k}, {m}, {kind}>", dict(key, wide=1)))
                 elif layout == 0:
